@@ -1,0 +1,15 @@
+"""FP64 CPU oracle of FRAM (arXiv 2508.00887).
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg to check and time the CUDA path.  The product
+package never imports it, and it imports nothing from the product package.
+"""
+from .fram_oracle import (DEFAULTS, DegenerateError, FramResult, InvalidInputError, SDSNResult,
+                          accuracy, damped_update, fram, gamma, gradient, initial_assignment,
+                          lap_max, matching_error, objective, p1, p2, p3, prescale, sdsn,
+                          validate)
+
+__all__ = ["DEFAULTS", "DegenerateError", "FramResult", "InvalidInputError", "SDSNResult",
+           "accuracy", "damped_update", "fram", "gamma", "gradient", "initial_assignment",
+           "lap_max", "matching_error", "objective", "p1", "p2", "p3", "prescale", "sdsn",
+           "validate"]
