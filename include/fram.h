@@ -1,0 +1,189 @@
+/*
+ * fram.h -- C ABI of the GB300 (sm_103a) FRAM solver.
+ *
+ * FRAM (Frobenius-Regularized Assignment Matching, arXiv 2508.00887) matches
+ * two undirected graphs with nonnegative symmetric adjacency matrices A and
+ * A~ (written B here) by the projected fixed-point iteration of eq. 3:
+ *
+ *     X     = A N B + lambda K                     (Alg. 1 step 5, eq. 3)
+ *     D     = SDSN(X, theta)                       (Alg. 1 step 6, Alg. 2)
+ *     N     = (1 - alpha) N + alpha D              (Alg. 1 step 7)
+ *     delta = ||N_t - N_{t-1}||_F / ||N_t||_F      (Alg. 1 step 8)
+ *
+ * until delta <= delta_tol, then rounds N to a permutation (eq. 2, Alg. 1
+ * step 10).  Every step runs in this library's own CUDA kernels.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ *  - Matrices are dense, row-major, contiguous n x n arrays of IEEE double.
+ *  - perm[i] (int32) is the node of the second graph matched to node i of
+ *    the first graph: the matching matrix has M[i][perm[i]] = 1.
+ *  - The caller owns every buffer it passes.  The library never frees or
+ *    keeps a caller pointer after the call returns (fram_submit copies its
+ *    inputs before returning).
+ *  - Pointer kinds: fram_solve and fram_solve_batched accept host or device
+ *    pointers for each matrix/vector argument (the kind is detected per
+ *    pointer); host buffers are staged through the context's device
+ *    workspace.  The step-level entry points (fram_gradient, fram_sdsn,
+ *    fram_assign) take device pointers only.
+ *  - All work is ordered on the context's stream.  Calls return after their
+ *    results are written (they synchronise that stream).
+ *  - Errors are reported by status code only; no exception or abort crosses
+ *    the ABI.  fram_last_error() gives a one-line description of the most
+ *    recent failure on a context.  Outputs are unspecified when a call fails.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef FRAM_H
+#define FRAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fram_ctx fram_ctx;
+
+typedef enum {
+  FRAM_OK = 0,
+  FRAM_NOT_READY = 1,       /* fram_poll: request still in flight            */
+  FRAM_ERR_INVALID = -1,    /* bad argument or input outside the graph model */
+  FRAM_ERR_OOM = -2,        /* workspace would exceed the HBM budget         */
+  FRAM_ERR_CUDA = -3,       /* a CUDA runtime call failed                    */
+  FRAM_ERR_DEGENERATE = -4, /* max(X) <= 0 in SDSN step 1 (e.g. no edges)    */
+  FRAM_ERR_TIMEOUT = -5,    /* a device-side wait exceeded its time limit    */
+  FRAM_ERR_BUSY = -6        /* fram_submit: admission queue is full          */
+} fram_status;
+
+typedef enum {
+  FRAM_PREC_FP64 = 0,       /* every step in FP64 (the parity path)                 */
+  FRAM_PREC_MIXED_TF32 = 1, /* TF32 tensor-core gradient, FP32 SDSN, FP64 update    */
+  FRAM_PREC_MIXED_BF16 = 2  /* BF16 tensor-core gradient, FP32 SDSN, FP64 update    */
+} fram_precision;
+
+/* Solver parameters.  fram_default_params() fills the paper's settings
+ * (Sec. 7 "Setting": lambda = 1, alpha = 0.95, theta = 10 for sparse graphs;
+ * use theta = 2 for dense ones) and the tolerances and caps that the paper
+ * leaves open. */
+typedef struct {
+  double lambda;      /* weight of the node term K (eq. 1); unused when K is NULL   */
+  double alpha;       /* damping step of eq. 3, in (0, 1]                           */
+  double theta;       /* FRA scale (Thm. 1); > 0                                    */
+  double delta_tol;   /* outer stop: delta <= delta_tol (default 1e-6)              */
+  double gamma_tol;   /* SDSN stop: gamma <= gamma_tol (default 1e-14)              */
+  double polish_tol;  /* mixed paths: FP64 polish runs while gamma > polish_tol     */
+  int max_outer;      /* outer-iteration cap (default 100)                          */
+  int max_sweeps;     /* SDSN sweep cap per call (default 200)                      */
+  int max_polish;     /* mixed paths: FP64 polish sweep cap per call (default 0)    */
+  int precision;      /* fram_precision                                             */
+  int init;           /* 0 = auto (N0 = 0 with K, 11^T/n without), 1 = zero, 2 = uniform */
+  int reserved;       /* must be 0                                                  */
+} fram_params;
+
+/* Per-solve diagnostics (all optional to read). */
+typedef struct {
+  int outer_iters;          /* outer iterations run                             */
+  int total_sweeps;         /* SDSN sweeps summed over the outer iterations     */
+  int polish_sweeps;        /* FP64 polish sweeps (mixed paths)                 */
+  int sdsn_converged_last;  /* 1 if the last SDSN call reached gamma_tol        */
+  int lap_augmentations;    /* rows placed by augmenting paths (0: argmax path) */
+  int reserved;
+  double delta;             /* last delta                                       */
+  double gamma;             /* gamma of the last SDSN output                    */
+  double objective;         /* Phi at the permutation, unscaled inputs (eq. 1)  */
+  double match_error;       /* 1/2 ||A - M B M^T||_F, unscaled (Sec. 7)         */
+  double assignment_value;  /* sum_i N[i][perm[i]] at the final N               */
+  double ms_total;          /* device time of the solve, milliseconds           */
+} fram_info;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device workspace the context may hold (0 = no cap).  `cuda_stream` is a
+ * cudaStream_t to order all work on, or NULL for a stream owned by the
+ * context.  Returns FRAM_ERR_INVALID for a bad device or NULL ctx pointer,
+ * FRAM_ERR_CUDA if the device cannot be used. */
+fram_status fram_create(fram_ctx **ctx, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Release the context and all device memory it holds.  NULL is a no-op. */
+fram_status fram_destroy(fram_ctx *ctx);
+
+/* Fill `p` with the defaults described at fram_params. */
+void fram_default_params(fram_params *p);
+
+/* Text of the last error on `ctx` ("" if none); valid until the next call. */
+const char *fram_last_error(const fram_ctx *ctx);
+
+/* Number of this library's kernels launched on `ctx` since creation. */
+uint64_t fram_kernel_launches(const fram_ctx *ctx);
+
+/* ------------------------------------------------------------ full solve */
+
+/* Solve one matching problem with FRAM (Alg. 1 + Alg. 2 + eq. 2).
+ *   n        number of nodes of each graph, n >= 1 (the paper's n = n~, Sec. 3)
+ *   A, B     n x n adjacency matrices: symmetric, nonnegative, finite
+ *            (Sec. 3 "Graph").  Host or device memory.
+ *   K        optional n x n node-similarity matrix K = F F~^T (eq. 1), or NULL.
+ *   params   solver parameters, or NULL for fram_default_params().
+ *   X_out    optional n x n output: the final soft assignment N.
+ *   perm_out n int32 outputs: the discretised matching (eq. 2).
+ *   info     optional diagnostics.
+ * Errors: FRAM_ERR_INVALID (n < 1, NULL A/B/perm_out, non-square shapes,
+ * asymmetric |A - A^T| > 1e-12 max(A, 1), negative or non-finite entries,
+ * bad params), FRAM_ERR_DEGENERATE (max(X) <= 0, e.g. edgeless graphs),
+ * FRAM_ERR_OOM, FRAM_ERR_TIMEOUT, FRAM_ERR_CUDA. */
+fram_status fram_solve(fram_ctx *ctx, int n, const double *A, const double *B, const double *K,
+                       const fram_params *params, double *X_out, int32_t *perm_out,
+                       fram_info *info);
+
+/* Solve `count` independent problems of (possibly different) sizes n[i] in
+ * one call.  Each problem follows fram_solve exactly (same parameters, no K).
+ * Problems with n[i] <= 64 run inside one persistent kernel, several per SM;
+ * larger ones run one after another through the single-problem path.
+ * Arrays of pointers are host arrays; the pointed-to matrices may be host or
+ * device memory.  X_out and infos may be NULL. */
+fram_status fram_solve_batched(fram_ctx *ctx, int count, const int *n, const double *const *A,
+                               const double *const *B, const fram_params *params,
+                               double *const *X_out, int32_t *const *perm_out, fram_info *infos);
+
+/* ------------------------------------------------------------- serving */
+
+/* Enqueue one problem for the context's continuous-batching scheduler.  A
+ * and B (host or device) are copied into library-owned device slots before
+ * the call returns.  Returns FRAM_ERR_BUSY when the request does not fit the
+ * HBM budget and the waiting queue is full. */
+fram_status fram_submit(fram_ctx *ctx, int n, const double *A, const double *B,
+                        const fram_params *params, uint64_t *ticket);
+
+/* Collect a submitted problem.  Waits up to wait_ms milliseconds (0 = do not
+ * wait, < 0 = wait until done).  Returns FRAM_NOT_READY while in flight;
+ * FRAM_OK copies N (if X_out != NULL), perm and info out and retires the
+ * ticket.  Unknown tickets give FRAM_ERR_INVALID. */
+fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *perm_out,
+                      fram_info *info, int wait_ms);
+
+/* ---------------------------------------------------- step-level entry points
+ * Single steps of the path on DEVICE buffers, for testing and composition. */
+
+/* Gradient of eq. 3 in FP64: X = A N B + lambda K (K may be NULL). */
+fram_status fram_gradient(fram_ctx *ctx, int n, const double *A, const double *N, const double *B,
+                          const double *K, double lambda, double *X);
+
+/* SDSN (Alg. 2) in FP64 on X, written to D (D may equal X):
+ * D0 = (theta/2) X / max(X); repeat D <- max(0, P1(D)) (eq. 7); stop when
+ * gamma = sum(D)/n - 1 <= gamma_tol or after max_sweeps sweeps.
+ * sweeps_out / gamma_out (host pointers) may be NULL.
+ * FRAM_ERR_DEGENERATE if max(X) <= 0. */
+fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double theta,
+                      double gamma_tol, int max_sweeps, int *sweeps_out, double *gamma_out);
+
+/* Linear assignment of eq. 2 on W (n x n, device): perm maximises
+ * sum_i W[i][perm[i]] (device int32 output).  value_out (host) may be NULL. */
+fram_status fram_assign(fram_ctx *ctx, int n, const double *W, int32_t *perm, double *value_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRAM_H */

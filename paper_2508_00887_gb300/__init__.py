@@ -1,0 +1,235 @@
+"""GB300 (sm_103a) FRAM solver: Python binding of the C ABI in ``include/fram.h``.
+
+This module only marshals arguments: every step of the solve (validation,
+prescaling, gradient GEMMs, SDSN, update, assignment, objective) runs in the
+CUDA kernels of ``libfram.so``.  There is no CPU fallback: if the library is
+missing, :func:`load` raises.
+
+Matrix arguments may be torch tensors (CUDA or CPU), numpy arrays, or raw
+integer addresses.  They must be contiguous ``float64`` (``int32`` for
+permutations).  Host and device buffers are both accepted by ``fram_solve``
+and ``fram_solve_batched``; the step-level calls take device buffers only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfram.so")
+
+FRAM_OK = 0
+FRAM_NOT_READY = 1
+FRAM_ERR_INVALID = -1
+FRAM_ERR_OOM = -2
+FRAM_ERR_CUDA = -3
+FRAM_ERR_DEGENERATE = -4
+FRAM_ERR_TIMEOUT = -5
+FRAM_ERR_BUSY = -6
+
+FRAM_PREC_FP64 = 0
+FRAM_PREC_MIXED_TF32 = 1
+FRAM_PREC_MIXED_BF16 = 2
+
+STATUS_NAMES = {0: "FRAM_OK", 1: "FRAM_NOT_READY", -1: "FRAM_ERR_INVALID", -2: "FRAM_ERR_OOM",
+                -3: "FRAM_ERR_CUDA", -4: "FRAM_ERR_DEGENERATE", -5: "FRAM_ERR_TIMEOUT",
+                -6: "FRAM_ERR_BUSY"}
+
+
+class FramParams(C.Structure):
+    _fields_ = [("lam", C.c_double), ("alpha", C.c_double), ("theta", C.c_double),
+                ("delta_tol", C.c_double), ("gamma_tol", C.c_double), ("polish_tol", C.c_double),
+                ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
+                ("precision", C.c_int), ("init", C.c_int), ("reserved", C.c_int)]
+
+
+class FramInfo(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("total_sweeps", C.c_int), ("polish_sweeps", C.c_int),
+                ("sdsn_converged_last", C.c_int), ("lap_augmentations", C.c_int),
+                ("reserved", C.c_int), ("delta", C.c_double), ("gamma", C.c_double),
+                ("objective", C.c_double), ("match_error", C.c_double),
+                ("assignment_value", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class FramError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load(path: str | None = None):
+    """Load ``libfram.so`` (built in-tree by ``paper_2508_00887_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_2508_00887_gb300.build`")
+    lib = C.CDLL(path)
+    i, d, u64, sz = C.c_int, C.c_double, C.c_uint64, C.c_size_t
+    sig = {
+        "fram_create": (i, [C.POINTER(_P), i, sz, _P]),
+        "fram_destroy": (i, [_P]),
+        "fram_default_params": (None, [C.POINTER(FramParams)]),
+        "fram_last_error": (C.c_char_p, [_P]),
+        "fram_kernel_launches": (u64, [_P]),
+        "fram_solve": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P, C.POINTER(FramInfo)]),
+        "fram_solve_batched": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P,
+                                   C.POINTER(FramInfo)]),
+        "fram_submit": (i, [_P, i, _P, _P, C.POINTER(FramParams), C.POINTER(u64)]),
+        "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
+        "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
+        "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
+        "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the header declares; used by the ABI test."""
+    return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
+            "fram_kernel_launches", "fram_solve", "fram_solve_batched", "fram_submit",
+            "fram_poll", "fram_gradient", "fram_sdsn", "fram_assign"]
+
+
+# ---------------------------------------------------------------- marshalling
+def _addr(x, dtype="float64"):
+    """Address of a contiguous buffer (torch tensor, numpy array or int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):            # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(x.dtype).split(".")[-1] != dtype:
+            raise ValueError(f"tensor dtype must be {dtype}, got {x.dtype}")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):              # numpy.ndarray
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if x.dtype.name != dtype:
+            raise ValueError(f"array dtype must be {dtype}, got {x.dtype}")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(ctx, status):
+    if status not in (FRAM_OK, FRAM_NOT_READY):
+        msg = load().fram_last_error(ctx)
+        raise FramError(status, msg.decode() if msg else "")
+    return status
+
+
+def fram_default_params(**overrides) -> FramParams:
+    p = FramParams()
+    load().fram_default_params(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def fram_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+    """Create a context; ``stream`` is a cudaStream_t address (e.g.
+    ``torch.cuda.current_stream().cuda_stream``) or None."""
+    ctx = _P()
+    st = load().fram_create(C.byref(ctx), device, hbm_budget_bytes, stream)
+    if st != FRAM_OK:
+        raise FramError(st, "fram_create failed")
+    return ctx
+
+
+def fram_destroy(ctx):
+    return load().fram_destroy(ctx)
+
+
+def fram_last_error(ctx) -> str:
+    m = load().fram_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def fram_kernel_launches(ctx) -> int:
+    return int(load().fram_kernel_launches(ctx))
+
+
+def fram_solve(ctx, n, A, B, K=None, params=None, X_out=None, perm_out=None, check=True):
+    info = FramInfo()
+    st = load().fram_solve(ctx, n, _addr(A), _addr(B), _addr(K),
+                           C.byref(params) if params is not None else None,
+                           _addr(X_out), _addr(perm_out, "int32"), C.byref(info))
+    if check:
+        _check(ctx, st)
+    return st, info
+
+
+def fram_solve_batched(ctx, ns, As, Bs, params=None, X_outs=None, perm_outs=None, check=True):
+    count = len(ns)
+    n_arr = (C.c_int * count)(*ns)
+    a_arr = (_P * count)(*[_addr(a) for a in As])
+    b_arr = (_P * count)(*[_addr(b) for b in Bs])
+    x_arr = (_P * count)(*[_addr(x) for x in X_outs]) if X_outs is not None else None
+    p_arr = (_P * count)(*[_addr(p, "int32") for p in perm_outs])
+    infos = (FramInfo * max(count, 1))()
+    st = load().fram_solve_batched(ctx, count, n_arr, a_arr, b_arr,
+                                   C.byref(params) if params is not None else None,
+                                   x_arr, p_arr, infos)
+    if check:
+        _check(ctx, st)
+    return st, list(infos)[:count]
+
+
+def fram_submit(ctx, n, A, B, params=None, check=True):
+    t = C.c_uint64()
+    st = load().fram_submit(ctx, n, _addr(A), _addr(B),
+                            C.byref(params) if params is not None else None, C.byref(t))
+    if check:
+        _check(ctx, st)
+    return st, t.value
+
+
+def fram_poll(ctx, ticket, X_out=None, perm_out=None, wait_ms=0, check=True):
+    info = FramInfo()
+    st = load().fram_poll(ctx, ticket, _addr(X_out), _addr(perm_out, "int32"), C.byref(info),
+                          wait_ms)
+    if check:
+        _check(ctx, st)
+    return st, info
+
+
+def fram_gradient(ctx, n, A, N, B, X, K=None, lam=1.0, check=True):
+    st = load().fram_gradient(ctx, n, _addr(A), _addr(N), _addr(B), _addr(K), lam, _addr(X))
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def fram_sdsn(ctx, n, X, D, theta, gamma_tol=1e-14, max_sweeps=200, check=True):
+    sw = C.c_int()
+    g = C.c_double()
+    st = load().fram_sdsn(ctx, n, _addr(X), _addr(D), theta, gamma_tol, max_sweeps, C.byref(sw),
+                          C.byref(g))
+    if check:
+        _check(ctx, st)
+    return st, sw.value, g.value
+
+
+def fram_assign(ctx, n, W, perm, check=True):
+    v = C.c_double()
+    st = load().fram_assign(ctx, n, _addr(W), _addr(perm, "int32"), C.byref(v))
+    if check:
+        _check(ctx, st)
+    return st, v.value

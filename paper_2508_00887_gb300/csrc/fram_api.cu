@@ -1,0 +1,517 @@
+// C ABI of the FRAM solver (include/fram.h): context, device workspace and
+// the host side of Alg. 1 (arXiv 2508.00887).  Every arithmetic step runs in
+// this library's kernels; the host only sequences launches and reads back a
+// few scalars per outer iteration (delta and the SDSN status).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fram.h"
+#include "fram_internal.cuh"
+#include "fram_ctx.h"
+
+using namespace fram;
+
+// ------------------------------------------------------------ helpers
+namespace fram {
+
+void set_err(fram_ctx* c, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->last_error = buf;
+}
+
+fram_status cuda_fail(fram_ctx* c, cudaError_t e, const char* what) {
+  set_err(c, "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return FRAM_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int round_ld(int n) { return ((n + 127) / 128) * 128; }
+
+static void dfree(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void Workspace::release() {
+  void** ptrs[] = {(void**)&As, (void**)&Bs, (void**)&Ks, (void**)&N, (void**)&T, (void**)&X,
+                   (void**)&A0, (void**)&B0, (void**)&K0, (void**)&perm, &lap_ws,
+                   (void**)&partials, (void**)&sdsn_partials, (void**)&scal, &mixed};
+  for (void** p : ptrs) dfree(*p);
+  if (hscal) cudaFreeHost(hscal);
+  hscal = nullptr;
+  cap_n = 0;
+  cap_ld = 0;
+  bytes = 0;
+}
+
+size_t Workspace::bytes_for(int n, int num_sms) {
+  const size_t ld = round_ld(n);
+  size_t b = 6 * ld * ld * sizeof(double);           // As Bs Ks N T X
+  b += 3 * (size_t)n * n * sizeof(double);           // staging of host inputs
+  b += (size_t)n * sizeof(int32_t) + lap_workspace_bytes(n);
+  b += 8192 * sizeof(double);
+  b += sdsn_partials_elems(n, num_sms) * sizeof(double);
+  b += mixed_bytes_for(n);
+  return b + 8 * 4096;
+}
+
+fram_status ensure_workspace(fram_ctx* c, int n) {
+  Workspace& w = c->ws;
+  if (n <= w.cap_n && w.scal != nullptr) return FRAM_OK;
+  const size_t need = Workspace::bytes_for(n, c->num_sms);
+  size_t others = c->serve_bytes;
+  if (c->budget && need + others > c->budget) {
+    set_err(c, "workspace for n=%d needs %zu bytes; HBM budget is %zu", n, need + others,
+            c->budget);
+    return FRAM_ERR_OOM;
+  }
+  w.release();
+  const size_t ld = round_ld(n);
+  const size_t mat = ld * ld * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes ? bytes : 256);
+  };
+  A((void**)&w.As, mat);
+  A((void**)&w.Bs, mat);
+  A((void**)&w.Ks, mat);
+  A((void**)&w.N, mat);
+  A((void**)&w.T, mat);
+  A((void**)&w.X, mat);
+  A((void**)&w.A0, (size_t)n * n * sizeof(double));
+  A((void**)&w.B0, (size_t)n * n * sizeof(double));
+  A((void**)&w.K0, (size_t)n * n * sizeof(double));
+  A((void**)&w.perm, (size_t)n * sizeof(int32_t));
+  A(&w.lap_ws, lap_workspace_bytes(n));
+  A((void**)&w.partials, 8192 * sizeof(double));
+  A((void**)&w.sdsn_partials, sdsn_partials_elems(n, c->num_sms) * sizeof(double));
+  A((void**)&w.scal, sizeof(DevScalars));
+  if (mixed_bytes_for(n)) A(&w.mixed, mixed_bytes_for(n));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&w.hscal, sizeof(DevScalars));
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.scal, 0, sizeof(DevScalars), c->stream);
+  if (e != cudaSuccess) {
+    w.release();
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) {
+      set_err(c, "cudaMalloc failed for n=%d workspace", n);
+      return FRAM_ERR_OOM;
+    }
+    return cuda_fail(c, e, "workspace allocation");
+  }
+  w.cap_n = n;
+  w.cap_ld = (int)ld;
+  w.bytes = need;
+  return FRAM_OK;
+}
+
+fram_status check_params(fram_ctx* c, const fram_params& p) {
+  if (!(p.alpha > 0.0 && p.alpha <= 1.0) || !(p.theta > 0.0) || !isfinite(p.theta) ||
+      !isfinite(p.lambda) || !(p.delta_tol >= 0.0) || !(p.gamma_tol == p.gamma_tol) ||
+      p.max_outer < 1 || p.max_sweeps < 1 || p.max_polish < 0 || p.init < 0 || p.init > 2 ||
+      p.precision < FRAM_PREC_FP64 || p.precision > FRAM_PREC_MIXED_BF16 || p.reserved != 0) {
+    set_err(c, "invalid fram_params");
+    return FRAM_ERR_INVALID;
+  }
+  return FRAM_OK;
+}
+
+// Map a device status word onto the ABI.
+fram_status dev_status(fram_ctx* c, int st, const char* where) {
+  if (st == DEV_OK) return FRAM_OK;
+  if (st == DEV_DEGENERATE) {
+    set_err(c, "%s: max(X) <= 0, SDSN step 1 is undefined", where);
+    return FRAM_ERR_DEGENERATE;
+  }
+  set_err(c, "%s: a device-side wait exceeded its limit", where);
+  return FRAM_ERR_TIMEOUT;
+}
+
+// Stage an n x n (or n) input: device pointers are used in place, host
+// buffers are copied into `staging`.
+fram_status stage_in(fram_ctx* c, const double* src, size_t count, double* staging,
+                     const double** out) {
+  if (src == nullptr) {
+    *out = nullptr;
+    return FRAM_OK;
+  }
+  if (is_device_ptr(src)) {
+    *out = src;
+    return FRAM_OK;
+  }
+  cudaError_t e = cudaMemcpyAsync(staging, src, count * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  *out = staging;
+  return FRAM_OK;
+}
+
+#define FR_TRY(x)                          \
+  do {                                     \
+    fram_status _s = (x);                  \
+    if (_s != FRAM_OK) return _s;          \
+  } while (0)
+#define FR_CUDA(x, what)                              \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+  } while (0)
+#define FR_LAUNCH(x, what)                                              \
+  do {                                                                  \
+    int _k = (x);                                                       \
+    if (_k < 0) return cuda_fail(c, cudaGetLastError(), what);          \
+    c->launches += (uint64_t)_k;                                        \
+  } while (0)
+
+// Validate inputs and prescale them (Alg. 1 steps 2-3).
+fram_status validate_and_scale(fram_ctx* c, int n, const double* A0, const double* B0,
+                               const double* K0, double* scale_c) {
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  FR_CUDA(cudaMemsetAsync(&w.scal->val, 0, sizeof(ValidateStats), c->stream), "memset");
+  FR_LAUNCH(launch_validate(A0, B0, K0, n, &w.scal->val, c->stream), "validate kernel");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->val, &w.scal->val, sizeof(ValidateStats),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  const ValidateStats& v = w.hscal->val;
+  const char* names[3] = {"A", "B", "K"};
+  for (int m = 0; m < 3; ++m)
+    if (v.bad_value[m]) {
+      set_err(c, "%s has negative or non-finite entries", names[m]);
+      return FRAM_ERR_INVALID;
+    }
+  double mx[3], as[2];
+  for (int m = 0; m < 3; ++m) memcpy(&mx[m], &v.maxbits[m], 8);
+  for (int m = 0; m < 2; ++m) memcpy(&as[m], &v.asymbits[m], 8);
+  for (int m = 0; m < 2; ++m)
+    if (as[m] > 1e-12 * std::max(mx[m], 1.0)) {
+      set_err(c, "%s is not symmetric (max |M - M^T| = %g)", names[m], as[m]);
+      return FRAM_ERR_INVALID;
+    }
+  double cc = std::max(mx[0], mx[1]);
+  if (K0) cc = std::max(cc, mx[2]);
+  if (!(cc > 0.0)) {
+    set_err(c, "all inputs are zero: SDSN step 1 is undefined");
+    return FRAM_ERR_DEGENERATE;
+  }
+  const double s = sqrt(cc);
+  FR_LAUNCH(launch_scale(A0, n, s, true, w.As, ld, c->stream), "scale kernel");
+  FR_LAUNCH(launch_scale(B0, n, s, true, w.Bs, ld, c->stream), "scale kernel");
+  if (K0) FR_LAUNCH(launch_scale(K0, n, cc, true, w.Ks, ld, c->stream), "scale kernel");
+  *scale_c = cc;
+  return FRAM_OK;
+}
+
+// The full single-pair solve on device-resident (or staged) inputs.
+fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, const double* K,
+                      const fram_params& p, double* X_out, int32_t* perm_out, fram_info* info) {
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  FR_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
+  const double *A0, *B0, *K0;
+  FR_TRY(stage_in(c, A, (size_t)n * n, w.A0, &A0));
+  FR_TRY(stage_in(c, B, (size_t)n * n, w.B0, &B0));
+  FR_TRY(stage_in(c, K, (size_t)n * n, w.K0, &K0));
+  double cc = 0.0;
+  FR_TRY(validate_and_scale(c, n, A0, B0, K0, &cc));
+
+  const bool zero_init = p.init == 1 || (p.init == 0 && K0 != nullptr);
+  FR_LAUNCH(launch_fill_assignment(w.N, n, ld, zero_init ? 0.0 : 1.0 / n, c->stream), "fill");
+
+  fram_info inf;
+  memset(&inf, 0, sizeof inf);
+  double delta = INFINITY;
+  fram_status rs = FRAM_OK;
+  if (p.precision == FRAM_PREC_FP64) {
+    for (int t = 0; t < p.max_outer; ++t) {
+      FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream),
+              "memset");
+      FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
+      FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
+      FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, K0 ? w.Ks : nullptr, p.lambda,
+                             &w.scal->xmax_key, c->stream),
+                "gemm");
+      SdsnLaunch L{};
+      L.n = n;
+      L.X = w.X;
+      L.ldx = ld;
+      L.Y = w.X;
+      L.ldy = ld;
+      L.theta = p.theta;
+      L.gamma_tol = p.gamma_tol;
+      L.max_sweeps = p.max_sweeps;
+      L.xmax_key = &w.scal->xmax_key;
+      L.stats = &w.scal->iter.sdsn;
+      L.partials = w.sdsn_partials;
+      L.barrier = &w.scal->bar;
+      L.limit_ns = c->wait_limit_ns;
+      FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+      FR_LAUNCH(launch_update(w.N, ld, w.X, ld, n, p.alpha, &w.scal->iter, w.partials,
+                              &w.scal->ticket_update, c->stream),
+                "update kernel");
+      FR_CUDA(cudaMemcpyAsync(&w.hscal->iter, &w.scal->iter, sizeof(IterStats),
+                              cudaMemcpyDeviceToHost, c->stream),
+              "readback");
+      FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+      const IterStats& it = w.hscal->iter;
+      FR_TRY(dev_status(c, it.sdsn.status, "SDSN"));
+      inf.outer_iters = t + 1;
+      inf.total_sweeps += it.sdsn.sweeps;
+      inf.sdsn_converged_last = it.sdsn.converged;
+      inf.gamma = it.sdsn.gamma;
+      delta = it.delta;
+      inf.delta = delta;
+      if (delta <= p.delta_tol) break;
+    }
+  } else {
+    rs = solve_mixed_loop(c, n, K0 != nullptr, p, &inf);
+    if (rs != FRAM_OK) return rs;
+  }
+
+  // Alg. 1 step 10 and eq. 1 on the unscaled inputs.
+  FR_LAUNCH(launch_lap(w.N, ld, n, w.perm, &w.scal->lap, w.lap_ws, c->stream), "lap kernels");
+  FR_LAUNCH(launch_objective(A0, B0, K0, p.lambda, n, w.perm, &w.scal->obj, w.partials,
+                             &w.scal->ticket_obj, c->stream),
+            "objective kernel");
+  if (X_out)
+    FR_CUDA(cudaMemcpy2DAsync(X_out, (size_t)n * sizeof(double), w.N, (size_t)ld * sizeof(double),
+                              (size_t)n * sizeof(double), n, cudaMemcpyDefault, c->stream),
+            "copy X_out");
+  FR_CUDA(cudaMemcpyAsync(perm_out, w.perm, (size_t)n * sizeof(int32_t), cudaMemcpyDefault,
+                          c->stream),
+          "copy perm_out");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->lap, &w.scal->lap, sizeof(LapStats) + sizeof(ObjStats),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  if (w.hscal->lap.status != 0) {
+    set_err(c, "assignment search did not terminate");
+    return FRAM_ERR_TIMEOUT;
+  }
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  inf.lap_augmentations = w.hscal->lap.augmented;
+  inf.assignment_value = w.hscal->lap.value;
+  inf.objective = w.hscal->obj.objective;
+  inf.match_error = w.hscal->obj.match_error;
+  inf.ms_total = ms;
+  if (info) *info = inf;
+  return FRAM_OK;
+}
+
+}  // namespace fram
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+void fram_default_params(fram_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->lambda = 1.0;
+  p->alpha = 0.95;
+  p->theta = 10.0;
+  p->delta_tol = 1e-6;
+  p->gamma_tol = 1e-14;
+  p->polish_tol = 1e-6;
+  p->max_outer = 100;
+  p->max_sweeps = 200;
+  p->max_polish = 0;
+  p->precision = FRAM_PREC_FP64;
+  p->init = 0;
+  p->reserved = 0;
+}
+
+fram_status fram_create(fram_ctx** out, int device, size_t budget, void* stream) {
+  if (!out) return FRAM_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return FRAM_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) return FRAM_ERR_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return FRAM_ERR_CUDA;
+  }
+  fram_ctx* c = new fram_ctx();
+  c->device = device;
+  c->budget = budget;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FRAM_ERR_CUDA;
+  } else {
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FRAM_ERR_CUDA;
+  }
+  *out = c;
+  return FRAM_OK;
+}
+
+fram_status fram_destroy(fram_ctx* c) {
+  if (!c) return FRAM_OK;
+  cudaSetDevice(c->device);
+  serve_shutdown(c);
+  cudaStreamSynchronize(c->stream);
+  c->ws.release();
+  batched_release(c);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+  return FRAM_OK;
+}
+
+const char* fram_last_error(const fram_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+uint64_t fram_kernel_launches(const fram_ctx* c) { return c ? c->launches : 0; }
+
+fram_status fram_solve(fram_ctx* c, int n, const double* A, const double* B, const double* K,
+                       const fram_params* params, double* X_out, int32_t* perm_out,
+                       fram_info* info) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !A || !B || !perm_out) {
+    set_err(c, "fram_solve: n >= 1 and non-NULL A, B, perm_out are required");
+    return FRAM_ERR_INVALID;
+  }
+  fram_params p;
+  if (params)
+    p = *params;
+  else
+    fram_default_params(&p);
+  FR_TRY(check_params(c, p));
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "set device");
+  std::lock_guard<std::mutex> lk(c->mu);
+  return solve_one(c, n, A, B, K, p, X_out, perm_out, info);
+}
+
+fram_status fram_gradient(fram_ctx* c, int n, const double* A, const double* Nm, const double* B,
+                          const double* K, double lambda, double* X) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !A || !Nm || !B || !X || !is_device_ptr(A) || !is_device_ptr(Nm) ||
+      !is_device_ptr(B) || !is_device_ptr(X) || (K && !is_device_ptr(K))) {
+    set_err(c, "fram_gradient: n >= 1 and device pointers A, N, B, X (and K) are required");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  FR_LAUNCH(launch_scale(A, n, 1.0, false, w.As, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(B, n, 1.0, false, w.Bs, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(Nm, n, 1.0, false, w.N, ld, c->stream), "copy");
+  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, false, w.Ks, ld, c->stream), "copy");
+  FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
+  FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, K ? w.Ks : nullptr, lambda, nullptr, c->stream),
+            "gemm");
+  FR_CUDA(cudaMemcpy2DAsync(X, (size_t)n * sizeof(double), w.X, (size_t)ld * sizeof(double),
+                            (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, c->stream),
+          "copy X");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  return FRAM_OK;
+}
+
+fram_status fram_sdsn(fram_ctx* c, int n, const double* X, double* D, double theta,
+                      double gamma_tol, int max_sweeps, int* sweeps_out, double* gamma_out) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !X || !D || !is_device_ptr(X) || !is_device_ptr(D) || !(theta > 0.0) ||
+      max_sweeps < 1) {
+    set_err(c, "fram_sdsn: n >= 1, device X and D, theta > 0, max_sweeps >= 1 are required");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream), "memset");
+  FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
+  FR_LAUNCH(launch_max(X, n, n, &w.scal->xmax_key, c->stream), "max kernel");
+  SdsnLaunch L{};
+  L.n = n;
+  L.X = X;
+  L.ldx = n;
+  L.Y = D;
+  L.ldy = n;
+  L.theta = theta;
+  L.gamma_tol = gamma_tol;
+  L.max_sweeps = max_sweeps;
+  L.xmax_key = &w.scal->xmax_key;
+  L.stats = &w.scal->iter.sdsn;
+  L.partials = w.sdsn_partials;
+  L.barrier = &w.scal->bar;
+  L.limit_ns = c->wait_limit_ns;
+  FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.sdsn, &w.scal->iter.sdsn, sizeof(SdsnStats),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  const SdsnStats& st = w.hscal->iter.sdsn;
+  FR_TRY(dev_status(c, st.status, "SDSN"));
+  if (sweeps_out) *sweeps_out = st.sweeps;
+  if (gamma_out) *gamma_out = st.gamma;
+  return FRAM_OK;
+}
+
+fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, double* value_out) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !W || !perm || !is_device_ptr(W) || !is_device_ptr(perm)) {
+    set_err(c, "fram_assign: n >= 1 and device W, perm are required");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  FR_LAUNCH(launch_lap(W, n, n, perm, &w.scal->lap, w.lap_ws, c->stream), "lap kernels");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->lap, &w.scal->lap, sizeof(LapStats), cudaMemcpyDeviceToHost,
+                          c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  if (w.hscal->lap.status != 0) {
+    set_err(c, "assignment search did not terminate");
+    return FRAM_ERR_TIMEOUT;
+  }
+  if (value_out) *value_out = w.hscal->lap.value;
+  return FRAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Host-side context and workspace of the FRAM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/fram.h"
+#include "fram_internal.cuh"
+
+namespace fram {
+
+// Device scalars of one solve.  `lap` and `obj` are adjacent: they are read
+// back with one copy.
+struct DevScalars {
+  IterStats iter;
+  ValidateStats val;
+  LapStats lap;
+  ObjStats obj;
+  unsigned long long xmax_key;
+  GridBarrier bar;
+  unsigned ticket_update;
+  unsigned ticket_obj;
+};
+
+// Device workspace of the single-pair path, grown on demand.  Matrices use a
+// leading dimension ld = n rounded up to 128 with zero padding.
+struct Workspace {
+  int cap_n = 0, cap_ld = 0;
+  size_t bytes = 0;
+  double *As = nullptr, *Bs = nullptr, *Ks = nullptr;  // prescaled inputs
+  double *N = nullptr, *T = nullptr, *X = nullptr;     // assignment, A*N, gradient/SDSN
+  double *A0 = nullptr, *B0 = nullptr, *K0 = nullptr;  // staged host inputs
+  int32_t* perm = nullptr;
+  void* lap_ws = nullptr;
+  double* partials = nullptr;       // block partials of update / objective
+  double* sdsn_partials = nullptr;  // SDSN row/column/tile partials
+  DevScalars* scal = nullptr;
+  DevScalars* hscal = nullptr;      // pinned host mirror
+  void* mixed = nullptr;            // low-precision shadows (mixed paths)
+  void release();
+  static size_t bytes_for(int n, int num_sms);
+};
+
+}  // namespace fram
+
+struct fram_ctx {
+  int device = 0, num_sms = 0, cc_major = 0, cc_minor = 0;
+  size_t budget = 0;
+  size_t serve_bytes = 0;  // device bytes held by serving slots
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string last_error;
+  uint64_t launches = 0;
+  uint64_t wait_limit_ns = fram::kWaitLimitNs;
+  std::mutex mu;
+  fram::Workspace ws;
+  void* batched = nullptr;
+  void* serve = nullptr;
+};
+
+namespace fram {
+
+void set_err(fram_ctx* c, const char* fmt, ...);
+fram_status cuda_fail(fram_ctx* c, cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+int round_ld(int n);
+fram_status ensure_workspace(fram_ctx* c, int n);
+fram_status check_params(fram_ctx* c, const fram_params& p);
+fram_status dev_status(fram_ctx* c, int st, const char* where);
+fram_status stage_in(fram_ctx* c, const double* src, size_t count, double* staging,
+                     const double** out);
+fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, const double* K,
+                      const fram_params& p, double* X_out, int32_t* perm_out, fram_info* info);
+
+// Mixed-precision outer loop (fram_mixed.cu).
+size_t mixed_bytes_for(int n);
+fram_status solve_mixed_loop(fram_ctx* c, int n, bool has_K, const fram_params& p,
+                             fram_info* inf);
+
+// Batched and serving state (fram_batched.cu, fram_serve.cu).
+void batched_release(fram_ctx* c);
+void serve_shutdown(fram_ctx* c);
+
+}  // namespace fram

@@ -1,0 +1,199 @@
+// Internal declarations shared by the FRAM CUDA translation units.
+// Nothing here is part of the public C ABI (include/fram.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fram {
+
+// Device-side status codes (written into a status word by kernels).
+enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_DEGENERATE = 2 };
+
+// Default limit for every device-side wait (grid barriers, flags).
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Max of nonnegative doubles through their bit patterns (monotone for +0..+inf).
+// -0.0 and negatives are mapped to +0 first.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  double c = v > 0.0 ? v : 0.0;
+  atomicMax(addr, (unsigned long long)__double_as_longlong(c));
+}
+
+// Order-preserving map of a double onto uint64 (for atomicMax of any sign);
+// key 0 sorts below every value and means "no value".
+__host__ __device__ __forceinline__ unsigned long long ordered_key(double v) {
+#ifdef __CUDA_ARCH__
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &v, 8);
+#endif
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__host__ __device__ __forceinline__ double from_ordered_key(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double v;
+  __builtin_memcpy(&v, &b, 8);
+  return v;
+#endif
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid.
+// State must be zeroed before the launch.  Every wait is limited in time:
+// on expiry the block records DEV_TIMEOUT, raises `abort`, and returns false;
+// blocks that see `abort` also return false.  Callers stop on false.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int abort;
+  int pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsigned& gen,
+                                          uint64_t limit_ns, int* status, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    __threadfence();
+    const unsigned prev = atomicAdd(&b->count, 1u);
+    if (prev == nblocks - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicExch(&b->gen, target);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (true) {
+        if ((int)(ld_acquire_u32(&b->gen) - target) >= 0) break;
+        if (ld_volatile_s32(&b->abort)) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > limit_ns) {
+          atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+          atomicExch(&b->abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(40);
+      }
+    }
+    __threadfence();
+    gen = target;
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// ------------------------------------------------------------ SDSN state
+struct SdsnStats {
+  int sweeps;
+  int converged;
+  int status;   // DevStatus
+  int pad;
+  double gamma;
+  double xmax;
+};
+
+// Per-iteration scalars of the outer loop, read back by the host.
+struct IterStats {
+  SdsnStats sdsn;
+  double delta;
+  double sum_d2;
+  double sum_n2;
+  int pad[2];
+};
+
+struct LapStats {
+  int augmented;
+  int status;
+  double value;
+};
+
+struct ObjStats {
+  double objective;
+  double match_error;
+};
+
+struct ValidateStats {
+  unsigned long long maxbits[3];   // max of A, B, K (nonneg doubles as bits)
+  unsigned long long asymbits[2];  // max |A - A^T|, |B - B^T|
+  int bad_value[3];                // negative or non-finite entries seen
+  int pad;
+};
+
+// ------------------------------------------------------------ launchers
+// Each returns the number of kernels it launched (>= 0) or -1 on a launch
+// error (cudaGetLastError() holds the cause).
+
+int launch_validate(const double* A, const double* B, const double* K, int n,
+                    ValidateStats* st, cudaStream_t s);
+int launch_scale(const double* src, int n, double inv, bool divide, double* dst, int ld,
+                 cudaStream_t s);
+int launch_fill_assignment(double* N, int n, int ld, double value, cudaStream_t s);
+int launch_dgemm(const double* A, const double* B, double* C, int ld, int n, const double* K,
+                 double lam, unsigned long long* cmax_bits, cudaStream_t s);
+int launch_max(const double* X, int ldx, int n, unsigned long long* key, cudaStream_t s);
+
+struct SdsnLaunch {
+  int n;
+  const void* X;  int ldx;     // FP64 or FP32 gradient
+  void* Y;        int ldy;     // output (may alias X)
+  double theta, gamma_tol;
+  int max_sweeps;
+  const unsigned long long* xmax_key;   // max(X) as an ordered key
+  SdsnStats* stats;
+  double* partials;            // workspace, sdsn_partials_elems(n, ...) doubles
+  GridBarrier* barrier;        // zeroed by the launcher
+  uint64_t limit_ns;
+};
+size_t sdsn_partials_elems(int n, int max_blocks);
+int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
+
+int launch_update(double* N, int ldn, const double* D, int ldd, int n, double alpha,
+                  IterStats* st, double* partials, unsigned* ticket, cudaStream_t s);
+size_t update_partials_elems(int n);
+
+int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
+               cudaStream_t s);
+size_t lap_workspace_bytes(int n);
+
+int launch_objective(const double* A, const double* B, const double* K, double lam, int n,
+                     const int32_t* perm, ObjStats* st, double* partials, unsigned* ticket,
+                     cudaStream_t s);
+
+}  // namespace fram
