@@ -182,6 +182,35 @@ fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double t
  * sum_i W[i][perm[i]] (device int32 output).  value_out (host) may be NULL. */
 fram_status fram_assign(fram_ctx *ctx, int n, const double *W, int32_t *perm, double *value_out);
 
+/* Largest n that fram_sdsn_static accepts. */
+#define FRAM_SDSN_STATIC_MAX_N 4096
+
+/* fram_sdsn without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- applications whose device memory belongs to another
+ * allocator (a framework's caching allocator or a pool reserved up front,
+ * which a foreign cudaMalloc would bypass or find empty) and loops that cannot
+ * afford the device-wide synchronisation of cudaFree.
+ *
+ * Same computation, kernel and launch configuration as fram_sdsn, on DEVICE
+ * buffers X and D (n x n row-major doubles, D may equal X), ordered on
+ * `cuda_stream` (NULL = legacy default stream); returns after the result is
+ * written.  No context is needed and nothing is allocated: the scratch (SDSN
+ * partials, grid barrier, max(X), status; about 2 MiB) is a static device
+ * array that every GPU loading this library holds until the process exits.
+ *  - n > FRAM_SDSN_STATIC_MAX_N returns FRAM_ERR_INVALID with a message.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents (each call clears what must start at zero).  Calls that overlap
+ *    on the GPU race on it: serialise them on one stream.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture begins.
+ * sweeps_out / gamma_out (host) may be NULL; `err` (host, err_len bytes, may
+ * be NULL) receives a one-line message on failure.  Other errors as fram_sdsn. */
+fram_status fram_sdsn_static(int n, const double *X, double *D, double theta, double gamma_tol,
+                             int max_sweeps, void *cuda_stream, int *sweeps_out, double *gamma_out,
+                             char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

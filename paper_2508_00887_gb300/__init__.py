@@ -88,6 +88,8 @@ def load(path: str | None = None):
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d)]),
+        "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
+                                 sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -101,7 +103,7 @@ def exported_symbols():
     """Names the header declares; used by the ABI test."""
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_gradient", "fram_sdsn", "fram_assign"]
+            "fram_poll", "fram_gradient", "fram_sdsn", "fram_assign", "fram_sdsn_static"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -225,6 +227,22 @@ def fram_sdsn(ctx, n, X, D, theta, gamma_tol=1e-14, max_sweeps=200, check=True):
     if check:
         _check(ctx, st)
     return st, sw.value, g.value
+
+
+FRAM_SDSN_STATIC_MAX_N = 4096
+
+
+def fram_sdsn_static(n, X, D, theta, gamma_tol=1e-14, max_sweeps=200, stream=None, check=True):
+    """Allocation-free SDSN (see include/fram.h): returns (status, sweeps, gamma, message)."""
+    sw = C.c_int()
+    g = C.c_double()
+    buf = C.create_string_buffer(256)
+    st = load().fram_sdsn_static(n, _addr(X), _addr(D), theta, gamma_tol, max_sweeps, stream,
+                                 C.byref(sw), C.byref(g), buf, 256)
+    msg = buf.value.decode()
+    if check and st != FRAM_OK:
+        raise FramError(st, msg)
+    return st, sw.value, g.value, msg
 
 
 def fram_assign(ctx, n, W, perm, check=True):
