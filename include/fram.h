@@ -73,6 +73,10 @@ typedef struct {
   double delta_tol;   /* outer stop: delta <= delta_tol (default 1e-6)              */
   double gamma_tol;   /* SDSN stop: gamma <= gamma_tol (default 1e-14)              */
   double polish_tol;  /* mixed paths: FP64 polish runs while gamma > polish_tol     */
+  double stall_ratio; /* mixed paths: also stop at the rounding floor, i.e. when     */
+  double stall_below; /* delta <= stall_below and delta > stall_ratio * previous     */
+                      /* delta (defaults 0.9 and 1e-3; stall_ratio = 0 disables).   */
+                      /* The FP64 path ignores both.                                 */
   int max_outer;      /* outer-iteration cap (default 100)                          */
   int max_sweeps;     /* SDSN sweep cap per call (default 200)                      */
   int max_polish;     /* mixed paths: FP64 polish sweep cap per call (default 0)    */
@@ -95,6 +99,10 @@ typedef struct {
   double match_error;       /* 1/2 ||A - M B M^T||_F, unscaled (Sec. 7)         */
   double assignment_value;  /* sum_i N[i][perm[i]] at the final N               */
   double ms_total;          /* device time of the solve, milliseconds           */
+  double ms_gemm;           /* device time in the gradient GEMMs (step 5)       */
+  double ms_sdsn;           /* device time in SDSN (step 6; FP32 phase if mixed)*/
+  double ms_polish;         /* device time in the FP64 polish (mixed paths)     */
+  double ms_update;         /* device time in the update + delta (steps 7-8)    */
 } fram_info;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -169,6 +177,15 @@ fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *pe
 /* Gradient of eq. 3 in FP64: X = A N B + lambda K (K may be NULL). */
 fram_status fram_gradient(fram_ctx *ctx, int n, const double *A, const double *N, const double *B,
                           const double *K, double lambda, double *X);
+
+/* Gradient of eq. 3 as the mixed paths form it: A, N, B (FP64, device) are
+ * rounded to BF16 (precision = FRAM_PREC_MIXED_BF16) or TF32
+ * (FRAM_PREC_MIXED_TF32); T = A N is accumulated in FP32 on the tensor cores
+ * and rounded to the same input format; X = T B (+ lambda K) is accumulated
+ * in FP32 and written as an n x n FP32 device array. */
+fram_status fram_gradient_lowp(fram_ctx *ctx, int n, const double *A, const double *N,
+                               const double *B, const double *K, double lambda, int precision,
+                               float *X);
 
 /* SDSN (Alg. 2) in FP64 on X, written to D (D may equal X):
  * D0 = (theta/2) X / max(X); repeat D <- max(0, P1(D)) (eq. 7); stop when

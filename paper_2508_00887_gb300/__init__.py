@@ -39,7 +39,7 @@ STATUS_NAMES = {0: "FRAM_OK", 1: "FRAM_NOT_READY", -1: "FRAM_ERR_INVALID", -2: "
 class FramParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("alpha", C.c_double), ("theta", C.c_double),
                 ("delta_tol", C.c_double), ("gamma_tol", C.c_double), ("polish_tol", C.c_double),
-                ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
+                ("stall_ratio", C.c_double), ("stall_below", C.c_double), ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("reserved", C.c_int)]
 
 
@@ -48,7 +48,9 @@ class FramInfo(C.Structure):
                 ("sdsn_converged_last", C.c_int), ("lap_augmentations", C.c_int),
                 ("reserved", C.c_int), ("delta", C.c_double), ("gamma", C.c_double),
                 ("objective", C.c_double), ("match_error", C.c_double),
-                ("assignment_value", C.c_double), ("ms_total", C.c_double)]
+                ("assignment_value", C.c_double), ("ms_total", C.c_double),
+                ("ms_gemm", C.c_double), ("ms_sdsn", C.c_double), ("ms_polish", C.c_double),
+                ("ms_update", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -86,6 +88,7 @@ def load(path: str | None = None):
         "fram_submit": (i, [_P, i, _P, _P, C.POINTER(FramParams), C.POINTER(u64)]),
         "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
+        "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d)]),
         "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
@@ -103,7 +106,8 @@ def exported_symbols():
     """Names the header declares; used by the ABI test."""
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_gradient", "fram_sdsn", "fram_assign", "fram_sdsn_static"]
+            "fram_poll", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_assign",
+            "fram_sdsn_static"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -214,6 +218,14 @@ def fram_poll(ctx, ticket, X_out=None, perm_out=None, wait_ms=0, check=True):
 
 def fram_gradient(ctx, n, A, N, B, X, K=None, lam=1.0, check=True):
     st = load().fram_gradient(ctx, n, _addr(A), _addr(N), _addr(B), _addr(K), lam, _addr(X))
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def fram_gradient_lowp(ctx, n, A, N, B, X, precision, K=None, lam=1.0, check=True):
+    st = load().fram_gradient_lowp(ctx, n, _addr(A), _addr(N), _addr(B), _addr(K), lam,
+                                   precision, _addr(X, "float32"))
     if check:
         _check(ctx, st)
     return st

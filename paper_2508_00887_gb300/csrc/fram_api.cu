@@ -64,6 +64,7 @@ void Workspace::release() {
   hscal = nullptr;
   cap_n = 0;
   cap_ld = 0;
+  mixed_cap_n = 0;
   bytes = 0;
 }
 
@@ -74,7 +75,6 @@ size_t Workspace::bytes_for(int n, int num_sms) {
   b += (size_t)n * sizeof(int32_t) + lap_workspace_bytes(n);
   b += 8192 * sizeof(double);
   b += sdsn_partials_elems(n, num_sms) * sizeof(double);
-  b += mixed_bytes_for(n);
   return b + 8 * 4096;
 }
 
@@ -109,7 +109,6 @@ fram_status ensure_workspace(fram_ctx* c, int n) {
   A((void**)&w.partials, 8192 * sizeof(double));
   A((void**)&w.sdsn_partials, sdsn_partials_elems(n, c->num_sms) * sizeof(double));
   A((void**)&w.scal, sizeof(DevScalars));
-  if (mixed_bytes_for(n)) A(&w.mixed, mixed_bytes_for(n));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&w.hscal, sizeof(DevScalars));
   if (e == cudaSuccess) e = cudaMemsetAsync(w.scal, 0, sizeof(DevScalars), c->stream);
   if (e != cudaSuccess) {
@@ -127,15 +126,48 @@ fram_status ensure_workspace(fram_ctx* c, int n) {
   return FRAM_OK;
 }
 
+// Low-precision buffers of the mixed paths, allocated on first use.
+fram_status ensure_mixed(fram_ctx* c, int n) {
+  Workspace& w = c->ws;
+  if (w.mixed != nullptr && n <= w.mixed_cap_n) return FRAM_OK;
+  if (w.mixed) cudaFree(w.mixed);
+  w.mixed = nullptr;
+  w.mixed_cap_n = 0;
+  const size_t need = mixed_bytes_for(n);
+  if (c->budget && w.bytes + need + c->serve_bytes > c->budget) {
+    set_err(c, "mixed-precision buffers for n=%d exceed the HBM budget", n);
+    return FRAM_ERR_OOM;
+  }
+  cudaError_t e = cudaMalloc(&w.mixed, need);
+  if (e != cudaSuccess) {
+    w.mixed = nullptr;
+    cudaGetLastError();
+    set_err(c, "cudaMalloc failed for mixed buffers (n=%d)", n);
+    return FRAM_ERR_OOM;
+  }
+  w.mixed_cap_n = n;
+  return FRAM_OK;
+}
+
 fram_status check_params(fram_ctx* c, const fram_params& p) {
   if (!(p.alpha > 0.0 && p.alpha <= 1.0) || !(p.theta > 0.0) || !isfinite(p.theta) ||
       !isfinite(p.lambda) || !(p.delta_tol >= 0.0) || !(p.gamma_tol == p.gamma_tol) ||
+      !(p.stall_ratio >= 0.0 && p.stall_ratio <= 1.0) || !(p.stall_below >= 0.0) ||
       p.max_outer < 1 || p.max_sweeps < 1 || p.max_polish < 0 || p.init < 0 || p.init > 2 ||
       p.precision < FRAM_PREC_FP64 || p.precision > FRAM_PREC_MIXED_BF16 || p.reserved != 0) {
     set_err(c, "invalid fram_params");
     return FRAM_ERR_INVALID;
   }
   return FRAM_OK;
+}
+
+double phase_ms(fram_ctx* c, int a, int b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->evp[a], c->evp[b]) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return ms;
 }
 
 // Map a device status word onto the ABI.
@@ -251,10 +283,12 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
       FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream),
               "memset");
       FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
+      FR_CUDA(cudaEventRecord(c->evp[0], c->stream), "event");
       FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
       FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, K0 ? w.Ks : nullptr, p.lambda,
                              &w.scal->xmax_key, c->stream),
                 "gemm");
+      FR_CUDA(cudaEventRecord(c->evp[1], c->stream), "event");
       SdsnLaunch L{};
       L.n = n;
       L.X = w.X;
@@ -270,9 +304,11 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
       L.barrier = &w.scal->bar;
       L.limit_ns = c->wait_limit_ns;
       FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+      FR_CUDA(cudaEventRecord(c->evp[2], c->stream), "event");
       FR_LAUNCH(launch_update(w.N, ld, w.X, ld, n, p.alpha, &w.scal->iter, w.partials,
                               &w.scal->ticket_update, c->stream),
                 "update kernel");
+      FR_CUDA(cudaEventRecord(c->evp[3], c->stream), "event");
       FR_CUDA(cudaMemcpyAsync(&w.hscal->iter, &w.scal->iter, sizeof(IterStats),
                               cudaMemcpyDeviceToHost, c->stream),
               "readback");
@@ -280,6 +316,9 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
       const IterStats& it = w.hscal->iter;
       FR_TRY(dev_status(c, it.sdsn.status, "SDSN"));
       inf.outer_iters = t + 1;
+      inf.ms_gemm += phase_ms(c, 0, 1);
+      inf.ms_sdsn += phase_ms(c, 1, 2);
+      inf.ms_update += phase_ms(c, 2, 3);
       inf.total_sweeps += it.sdsn.sweeps;
       inf.sdsn_converged_last = it.sdsn.converged;
       inf.gamma = it.sdsn.gamma;
@@ -288,6 +327,7 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
       if (delta <= p.delta_tol) break;
     }
   } else {
+    FR_TRY(ensure_mixed(c, n));
     rs = solve_mixed_loop(c, n, K0 != nullptr, p, &inf);
     if (rs != FRAM_OK) return rs;
   }
@@ -338,6 +378,8 @@ void fram_default_params(fram_params* p) {
   p->delta_tol = 1e-6;
   p->gamma_tol = 1e-14;
   p->polish_tol = 1e-6;
+  p->stall_ratio = 0.9;
+  p->stall_below = 1e-3;
   p->max_outer = 100;
   p->max_sweeps = 200;
   p->max_polish = 0;
@@ -375,7 +417,9 @@ fram_status fram_create(fram_ctx** out, int device, size_t budget, void* stream)
   } else {
     c->own_stream = true;
   }
-  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+  bool ev_ok = cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+  for (int i = 0; i < 5 && ev_ok; ++i) ev_ok = cudaEventCreate(&c->evp[i]) == cudaSuccess;
+  if (!ev_ok) {
     cudaGetLastError();
     delete c;
     return FRAM_ERR_CUDA;
@@ -393,6 +437,8 @@ fram_status fram_destroy(fram_ctx* c) {
   batched_release(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (int i = 0; i < 5; ++i)
+    if (c->evp[i]) cudaEventDestroy(c->evp[i]);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;
@@ -447,6 +493,44 @@ fram_status fram_gradient(fram_ctx* c, int n, const double* A, const double* Nm,
                             (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, c->stream),
           "copy X");
   FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  return FRAM_OK;
+}
+
+fram_status fram_gradient_lowp(fram_ctx* c, int n, const double* A, const double* Nm,
+                               const double* B, const double* K, double lambda, int precision,
+                               float* X) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !A || !Nm || !B || !X || !is_device_ptr(A) || !is_device_ptr(Nm) ||
+      !is_device_ptr(B) || !is_device_ptr(X) || (K && !is_device_ptr(K)) ||
+      (precision != FRAM_PREC_MIXED_BF16 && precision != FRAM_PREC_MIXED_TF32)) {
+    set_err(c, "fram_gradient_lowp: n >= 1, device A, N, B, X (and K), and a mixed precision "
+               "are required");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  FR_TRY(ensure_mixed(c, n));
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  FR_LAUNCH(launch_scale(A, n, 1.0, false, w.As, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(B, n, 1.0, false, w.Bs, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(Nm, n, 1.0, false, w.N, ld, c->stream), "copy");
+  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, false, w.Ks, ld, c->stream), "copy");
+  float* X32 = nullptr;
+  FR_TRY(mixed_gradient(c, n, K != nullptr, lambda, precision == FRAM_PREC_MIXED_BF16 ? 0 : 1,
+                        &X32));
+  FR_CUDA(cudaMemcpy2DAsync(X, (size_t)n * sizeof(float), X32, (size_t)ld * sizeof(float),
+                            (size_t)n * sizeof(float), n, cudaMemcpyDeviceToDevice, c->stream),
+          "copy X");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.gemm_err, &w.scal->iter.gemm_err, sizeof(int),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  if (w.hscal->iter.gemm_err) {
+    set_err(c, "tensor-core GEMM: a device-side wait exceeded its limit");
+    return FRAM_ERR_TIMEOUT;
+  }
   return FRAM_OK;
 }
 

@@ -39,6 +39,7 @@ struct Workspace {
   DevScalars* scal = nullptr;
   DevScalars* hscal = nullptr;      // pinned host mirror
   void* mixed = nullptr;            // low-precision shadows (mixed paths)
+  int mixed_cap_n = 0;
   void release();
   static size_t bytes_for(int n, int num_sms);
 };
@@ -52,6 +53,7 @@ struct fram_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evp[5] = {};  // phase boundaries inside one outer iteration
   std::string last_error;
   uint64_t launches = 0;
   uint64_t wait_limit_ns = fram::kWaitLimitNs;
@@ -68,8 +70,11 @@ fram_status cuda_fail(fram_ctx* c, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
 int round_ld(int n);
 fram_status ensure_workspace(fram_ctx* c, int n);
+fram_status ensure_mixed(fram_ctx* c, int n);
 fram_status check_params(fram_ctx* c, const fram_params& p);
 fram_status dev_status(fram_ctx* c, int st, const char* where);
+// Elapsed ms between phase events a and b of the current iteration.
+double phase_ms(fram_ctx* c, int a, int b);
 fram_status stage_in(fram_ctx* c, const double* src, size_t count, double* staging,
                      const double** out);
 fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, const double* K,
@@ -79,6 +84,7 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
 size_t mixed_bytes_for(int n);
 fram_status solve_mixed_loop(fram_ctx* c, int n, bool has_K, const fram_params& p,
                              fram_info* inf);
+fram_status mixed_gradient(fram_ctx* c, int n, bool has_K, double lam, int kind, float** X32);
 
 // Batched and serving state (fram_batched.cu, fram_serve.cu).
 void batched_release(fram_ctx* c);

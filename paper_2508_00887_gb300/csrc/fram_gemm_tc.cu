@@ -1,0 +1,403 @@
+// Tensor-core gradient GEMMs of the mixed-precision path (Alg. 1 step 5,
+// eq. 3 of arXiv 2508.00887; the paper runs this step in TF32):
+//
+//   C[i][j] = sum_k A[i][k] * Bop[j][k]      (both operands K-major)
+//
+// Used twice per outer iteration: T = A_s * N (Bop = N^T, written transposed
+// by the update kernel) and X = T * B_s (+ lambda K) (Bop = B_s, symmetric).
+// Inputs are BF16 (tcgen05.mma kind::f16) or TF32-rounded FP32 (kind::tf32);
+// accumulation is FP32 in tensor memory.
+//
+// One CTA computes one 128 x 128 output tile:
+//   warp 0     TMA producer: 128-byte-swizzled A/B k-slices into a 4-stage
+//              shared-memory ring (mbarrier full/empty pairs)
+//   warp 1     allocates 128 TMEM columns; one elected thread issues the
+//              tcgen05.mma instructions (M=128, N=128, K=16 or 8 each) and
+//              commits each stage back to its empty barrier
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (each warp reads its
+//              own 32-lane quarter of TMEM), optional + lambda K, max(C), and
+//              the store in the output precision
+// Every mbarrier wait is limited in time; on expiry the kernel records an
+// error, drains its own TMA copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "fram_internal.cuh"
+#include "fram_tc.h"
+
+namespace fram {
+
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int ROW_BYTES = 128;              // one swizzle atom row per k-slice
+constexpr int STAGES = 4;
+constexpr int TILE_BYTES = BM * ROW_BYTES;  // 16 KiB per operand per stage
+constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int GEMM_THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+struct GemmArgs {
+  int ld;                  // M = N = K = ld (multiple of 128)
+  int n;                   // valid rows/cols for the K term and the max
+  int kind;                // 0: BF16 operands, 1: TF32 operands
+  int out_kind;            // 0: FP32, 1: BF16, 2: TF32-rounded FP32
+  void* C;
+  const double* Kmat;      // optional lambda K term (FP64, ld-strided)
+  double lam;
+  unsigned long long* cmax;  // optional ordered-key max over n x n
+  int* err;
+  uint64_t limit_ns;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor, K-major, 128-byte swizzle:
+// start address >> 4 in bits [0,14), stride byte offset (8 rows x 128 B) >> 4
+// in [32,46), descriptor version 1 in [46,48), layout SWIZZLE_128B (2) in [61,64).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator (bits [4,6) = 1), A/B format in
+// [7,10)/[10,13) (BF16 = 1, TF32 = 2), both K-major, N >> 3 in [17,23),
+// M >> 4 in [24,29).
+__host__ __device__ constexpr uint32_t instr_desc(int kind) {
+  return (1u << 4) | ((kind == 0 ? 1u : 2u) << 7) | ((kind == 0 ? 1u : 2u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ float s_max[4];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (raw & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES, done = empty0 + 8 * STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* s_consumed = s_fail + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  constexpr int KELEMS = KIND == 0 ? 64 : 32;     // elements per 128-byte row
+  constexpr int UMMA_K_BYTES = 32;                 // K=16 BF16 or K=8 TF32 per MMA
+  const int nkb = g.ld / KELEMS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    *s_fail = 0;
+    *s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1, g.limit_ns)) {
+          *s_fail = 1;
+          break;
+        }
+        if (*s_fail) break;
+        const uint32_t fb = full0 + 8 * s;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        tma_load_2d(sbase + s * STAGE_BYTES, &tmA, kb * KELEMS, m0, fb);
+        tma_load_2d(sbase + s * STAGE_BYTES + TILE_BYTES, &tmB, kb * KELEMS, n0, fb);
+        issued = kb + 1;
+      }
+      if (*s_fail) {
+        // Drain: wait (limited) for our own copies that nobody consumed.
+        const int consumed = *s_consumed;
+        for (int kb = consumed; kb < issued; ++kb)
+          mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, g.limit_ns);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(KIND);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, g.limit_ns) || *s_fail) {
+          *s_fail = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_addr = sbase + s * STAGE_BYTES;
+        const uint32_t b_addr = a_addr + TILE_BYTES;
+#pragma unroll
+        for (int k = 0; k < ROW_BYTES / UMMA_K_BYTES; ++k) {
+          mma<KIND>(tmem, smem_desc_sw128(a_addr + k * UMMA_K_BYTES),
+                    smem_desc_sw128(b_addr + k * UMMA_K_BYTES), idesc, (kb | k) != 0 ? 1u : 0u);
+        }
+        mma_commit(empty0 + 8 * s);
+        *s_consumed = kb + 1;
+      }
+      // Signal the epilogue; on failure this still tracks the MMAs issued so
+      // far, so TMEM is only released after they finish.
+      mma_commit(done);
+      if (!ok) mbar_wait(done, 0, g.limit_ns);
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = m0 + q * 32 + lane;
+    float lmax = -INFINITY;
+    const bool ready = mbar_wait(done, 0, g.limit_ns) && !*s_fail;
+    if (!ready) *s_fail = 1;
+    if (ready) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+        const int col0 = n0 + c0;
+        if (g.Kmat != nullptr && row < g.n) {
+          const double* kr = g.Kmat + (size_t)row * g.ld + col0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (col0 + i < g.n) v[i] += (float)(g.lam * kr[i]);
+        }
+        if (g.cmax != nullptr && row < g.n) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (col0 + i < g.n) lmax = fmaxf(lmax, v[i]);
+        }
+        if (g.out_kind == 1) {
+          __nv_bfloat162 h[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(g.C) +
+                                                (size_t)row * g.ld + col0);
+          dst[0] = *reinterpret_cast<uint4*>(&h[0]);
+          dst[1] = *reinterpret_cast<uint4*>(&h[4]);
+        } else {
+          if (g.out_kind == 2) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = to_tf32(v[i]);
+          }
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(g.C) + (size_t)row * g.ld +
+                                                  col0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2],
+                                                           v[4 * i + 3]);
+        }
+      }
+    }
+    if (g.cmax != nullptr) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      if (lane == 0) s_max[warp - 2] = lmax;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                 : "memory");
+  }
+  if (threadIdx.x == 0) {
+    if (*s_fail) atomicExch(g.err, DEV_TIMEOUT);
+    if (g.cmax != nullptr && !*s_fail) {
+      const float m = fmaxf(fmaxf(s_max[0], s_max[1]), fmaxf(s_max[2], s_max[3]));
+      if (m > -INFINITY) atomicMax(g.cmax, ordered_key((double)m));
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, int ld, int kind) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const size_t es = kind == 0 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es), (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   2, const_cast<void*>(ptr), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int kind, int out_kind,
+                   const double* Kmat, double lam, unsigned long long* cmax, int* err,
+                   uint64_t limit_ns, cudaStream_t s) {
+  if (ld % 128 != 0 || ld <= 0) return -1;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bop) |
+       reinterpret_cast<uintptr_t>(C)) & 15)
+    return -1;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, ld, kind) || !make_map(&mb, Bop, ld, kind)) return -1;
+  GemmArgs g{};
+  g.ld = ld;
+  g.n = n;
+  g.kind = kind;
+  g.out_kind = out_kind;
+  g.C = C;
+  g.Kmat = Kmat;
+  g.lam = lam;
+  g.cmax = cmax;
+  g.err = err;
+  g.limit_ns = limit_ns;
+  dim3 grid(ld / BN, ld / BM);
+  if (kind == 0) {
+    static bool attr0 = false;
+    if (!attr0) {
+      if (cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMEM_BYTES) != cudaSuccess)
+        return -1;
+      attr0 = true;
+    }
+    gemm_tc_kernel<0><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
+  } else {
+    static bool attr1 = false;
+    if (!attr1) {
+      if (cudaFuncSetAttribute(gemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMEM_BYTES) != cudaSuccess)
+        return -1;
+      attr1 = true;
+    }
+    gemm_tc_kernel<1><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace fram

@@ -131,11 +131,13 @@ struct SdsnStats {
 
 // Per-iteration scalars of the outer loop, read back by the host.
 struct IterStats {
-  SdsnStats sdsn;
+  SdsnStats sdsn;     // SDSN of this iteration (FP64 path) or its FP32 phase (mixed)
+  SdsnStats polish;   // FP64 polish phase (mixed paths)
   double delta;
   double sum_d2;
   double sum_n2;
-  int pad[2];
+  int gemm_err;       // tensor-core GEMM wait expired (mixed paths)
+  int pad;
 };
 
 struct LapStats {
@@ -172,10 +174,15 @@ int launch_max(const double* X, int ldx, int n, unsigned long long* key, cudaStr
 struct SdsnLaunch {
   int n;
   const void* X;  int ldx;     // FP64 or FP32 gradient
-  void* Y;        int ldy;     // output (may alias X)
+  void* Y;        int ldy;     // output (may alias X when the types match)
+  int in_fp32 = 0;             // X is FP32
+  int out_fp32 = 0;            // Y and the sweep arithmetic are FP32
+  int mode = 0;                // 0: scale X (Alg. 2 step 1); 1: continue from Y0 = X
   double theta, gamma_tol;
   int max_sweeps;
-  const unsigned long long* xmax_key;   // max(X) as an ordered key
+  const unsigned long long* xmax_key;   // max(X) as an ordered key (mode 0)
+  const SdsnStats* gate = nullptr;      // skip the sweeps if gate->gamma <= gate_tol
+  double gate_tol = 0.0;
   SdsnStats* stats;
   double* partials;            // workspace, sdsn_partials_elems(n, ...) doubles
   GridBarrier* barrier;        // zeroed by the launcher
@@ -183,6 +190,7 @@ struct SdsnLaunch {
 };
 size_t sdsn_partials_elems(int n, int max_blocks);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
+int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 
 int launch_update(double* N, int ldn, const double* D, int ldd, int n, double alpha,
                   IterStats* st, double* partials, unsigned* ticket, cudaStream_t s);

@@ -4,13 +4,6 @@
 
 namespace fram {
 
-size_t mixed_bytes_for(int) { return 0; }
-
-fram_status solve_mixed_loop(fram_ctx* c, int, bool, const fram_params&, fram_info*) {
-  set_err(c, "mixed precision path is not available in this build");
-  return FRAM_ERR_INVALID;
-}
-
 void batched_release(fram_ctx*) {}
 void serve_shutdown(fram_ctx*) {}
 

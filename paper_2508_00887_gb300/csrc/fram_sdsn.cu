@@ -9,13 +9,15 @@
 //
 // Layout: the n x n matrix is cut into a P x Q grid of tiles, one CTA per
 // tile.  Each sweep reads the tile once and writes it once; the same pass
-// accumulates the new tile's row sums, column sums and total, which the CTA
-// publishes as partials (double-buffered by sweep parity).  After one grid
-// barrier every CTA combines the Q row partials of its rows, the P column
-// partials of its columns and the P*Q totals, always in the same order, so
-// all CTAs agree bit for bit on S, on gamma and therefore on when to stop.
-// When the tile fits in shared memory it stays there for all sweeps and
-// global memory is touched only to load X and to store the result.
+// accumulates the new tile's row sums (warp shuffles), column sums (per-lane
+// registers, combined across warps in shared memory) and total, which the
+// CTA publishes as partials, double-buffered by sweep parity.  After one
+// grid barrier every CTA loads the Q row partials of its rows, the P column
+// partials of its columns and all P*Q totals with independent loads (a
+// single L2 round trip), and combines them in a fixed order, so every CTA
+// agrees bit for bit on S, on gamma and therefore on when to stop.  When the
+// tile fits in shared memory it stays there for all sweeps, and global
+// memory is touched only to load X and to store the result.
 #include <math.h>
 
 #include "fram_internal.cuh"
@@ -27,23 +29,27 @@ namespace {
 constexpr int kSdsnThreads = 512;
 constexpr int kSdsnWarps = kSdsnThreads / 32;
 constexpr size_t kSmemCap = 200 * 1024;
+constexpr int kMaxGrid = 16;  // P, Q <= 16 (gather unrolled to this bound)
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-template <typename T>
+template <typename T, typename TIn>
 struct SdsnK {
   int n, P, Q, tr, tc, resident;
-  const T* X;
+  int mode;  // 0: Y0 = (theta/2) X / max(X) (Alg. 2 step 1); 1: Y0 = X (continue a run)
+  const TIn* X;
   int ldx;
   T* Y;
   int ldy;
   double theta, gamma_tol;
   int max_sweeps;
   const unsigned long long* xmax_key;
+  const SdsnStats* gate;  // optional: run no sweep if gate->gamma <= gate_tol
+  double gate_tol;
   SdsnStats* stats;
-  double* rpart;  // [2][Q][n]
-  double* cpart;  // [2][P][n]
-  double* tpart;  // [2][P*Q]
+  T* rpart;       // [2][Q][n] row partials (sweep arithmetic type)
+  T* cpart;       // [2][P][n] column partials
+  double* tpart;  // [2][P*Q] tile totals (S and gamma are always FP64)
   GridBarrier* bar;
   uint64_t limit_ns;
 };
@@ -52,69 +58,137 @@ template <typename T>
 __host__ __device__ inline size_t sdsn_smem_bytes(int tr, int tc, bool resident) {
   size_t b = 0;
   if (resident) b += align16((size_t)tr * tc * sizeof(T));
-  b += align16((size_t)kSdsnWarps * tc * sizeof(T));  // column accumulators
-  b += align16((size_t)tr * sizeof(double));           // row sums of the tile
+  b += align16((size_t)kSdsnWarps * tc * sizeof(T));  // per-warp column sums
+  b += align16((size_t)tr * sizeof(T));                // row sums of the tile
   b += align16((size_t)tr * sizeof(T));                // a_i = 1/n + S/n^2 - r_i/n
   b += align16((size_t)tc * sizeof(T));                // b_j = c_j/n
   return b;
 }
 
-// One pass over the tile.  FIRST: Y = (theta/2) X / m.  Otherwise the fused
-// P1+P2 sweep.  Both accumulate the new tile's sums and publish them into
-// partial buffer `wb`.
-template <typename T, bool FIRST>
-__device__ __forceinline__ void sdsn_pass(const SdsnK<T>& p, T* tile, int ldt, T* colacc,
-                                          double* rowsum, const T* arow, const T* bcol, int nr,
-                                          int nc, int r0, int c0, int bi, int bj, double half_theta,
-                                          double m, int wb) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < kSdsnWarps * p.tc; e += kSdsnThreads) colacc[e] = T(0);
+// max(0, y) without a floating-point instruction: clear y if its sign bit
+// is set (IEEE: every value with the sign bit set is <= 0, NaN excluded).
+__device__ __forceinline__ double relu(double y) {
+  const long long b = __double_as_longlong(y);
+  return __longlong_as_double(b & ~(b >> 63));
+}
+__device__ __forceinline__ float relu(float y) {
+  const int b = __float_as_int(y);
+  return __int_as_float(b & ~(b >> 31));
+}
+
+// Barrier on a counter that only grows: the k-th barrier of the launch waits
+// until the counter reaches k * nblocks.  Time-limited (see GridBarrier).
+__device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
+                                                uint64_t limit_ns, int* status, int* s_flag) {
   __syncthreads();
-  T* cacc = colacc + warp * p.tc;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
+    if ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+      const uint64_t t0 = globaltimer_ns();
+      unsigned polls = 0;
+      while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+        if ((++polls & 63u) == 0) {
+          if (ld_volatile_s32(&b->abort)) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer_ns() - t0 > limit_ns) {
+            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+            atomicExch(&b->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// One pass over the tile.  FIRST: Y = (theta/2) X / m (mode 0) or Y = X
+// (mode 1).  Otherwise the fused P1+P2 sweep.  Both accumulate the new
+// tile's sums and publish them into partial buffer `wb`.  MAXC > 0: lane l
+// owns columns l + 32 s (s < MAXC) and keeps their sums in registers;
+// MAXC == 0: per-warp column sums accumulate in shared memory.
+template <typename T, typename TIn, int MAXC, bool FIRST>
+__device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int ldt, T* colacc,
+                                          T* rowsum, const T* arow, const T* bcol, int nr,
+                                          int nc, int r0, int c0, int bi, int bj, T scale, int wb) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* wacc = colacc + warp * p.tc;
+  if (MAXC == 0)
+    for (int j = lane; j < nc; j += 32) wacc[j] = T(0);
+  T cacc[MAXC > 0 ? MAXC : 1];
+#pragma unroll
+  for (int s = 0; s < (MAXC > 0 ? MAXC : 1); ++s) cacc[s] = T(0);
+
   for (int i = warp; i < nr; i += kSdsnWarps) {
     T* row = tile + (size_t)i * ldt;
+    const TIn* xrow = FIRST ? p.X + (size_t)(r0 + i) * p.ldx + c0 : nullptr;
+    T ai = T(0);
+    if (!FIRST) ai = arow[i];
     T racc = T(0);
-    if (FIRST) {
-      const T* xrow = p.X + (size_t)(r0 + i) * p.ldx + c0;
-      for (int j = lane; j < nc; j += 32) {
-        const T y = (T)(half_theta * ((double)xrow[j] / m));
-        row[j] = y;
-        racc += y;
-        cacc[j] += y;
+    if (MAXC > 0) {
+#pragma unroll
+      for (int s = 0; s < MAXC; ++s) {
+        const int j = lane + 32 * s;
+        if (j < nc) {
+          T y;
+          if (FIRST)
+            y = p.mode == 0 ? (T)xrow[j] * scale : (T)xrow[j];
+          else
+            y = relu((row[j] + ai) - bcol[j]);
+          row[j] = y;
+          racc += y;
+          cacc[s] += y;
+        }
       }
     } else {
-      const T ai = arow[i];
       for (int j = lane; j < nc; j += 32) {
-        T y = (row[j] + ai) - bcol[j];
-        y = y > T(0) ? y : T(0);
+        T y;
+        if (FIRST)
+          y = p.mode == 0 ? (T)xrow[j] * scale : (T)xrow[j];
+        else
+          y = relu((row[j] + ai) - bcol[j]);
         row[j] = y;
         racc += y;
-        cacc[j] += y;
+        wacc[j] += y;
       }
     }
     racc = warp_sum(racc);
-    if (lane == 0) rowsum[i] = (double)racc;
+    if (lane == 0) rowsum[i] = racc;
+  }
+  if (MAXC > 0) {
+#pragma unroll
+    for (int s = 0; s < MAXC; ++s) {
+      const int j = lane + 32 * s;
+      if (j < nc) wacc[j] = cacc[s];  // zeros for warps that had no row
+    }
   }
   __syncthreads();
-  double* rp = p.rpart + ((size_t)wb * p.Q + bj) * p.n + r0;
+  T* rp = p.rpart + ((size_t)wb * p.Q + bj) * p.n + r0;
   for (int i = tid; i < nr; i += kSdsnThreads) rp[i] = rowsum[i];
-  double* cp = p.cpart + ((size_t)wb * p.P + bi) * p.n + c0;
+  T* cp = p.cpart + ((size_t)wb * p.P + bi) * p.n + c0;
   for (int j = tid; j < nc; j += kSdsnThreads) {
-    double c = 0.0;
-#pragma unroll 4
-    for (int w = 0; w < kSdsnWarps; ++w) c += (double)colacc[w * p.tc + j];
+    T c = T(0);
+#pragma unroll
+    for (int w = 0; w < kSdsnWarps; ++w) c += colacc[w * p.tc + j];
     cp[j] = c;
   }
   if (warp == 0) {
     double t = 0.0;
-    for (int i = lane; i < nr; i += 32) t += rowsum[i];
+    for (int i = lane; i < nr; i += 32) t += (double)rowsum[i];
     t = warp_sum(t);
     if (lane == 0) p.tpart[(size_t)wb * gridDim.x + blockIdx.x] = t;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T> p) {
+template <typename T, typename TIn, int MAXC>
+__global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ double s_S;
@@ -137,15 +211,16 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T> p) {
   }
   T* colacc = reinterpret_cast<T*>(smem + off);
   off += align16((size_t)kSdsnWarps * p.tc * sizeof(T));
-  double* rowsum = reinterpret_cast<double*>(smem + off);
-  off += align16((size_t)p.tr * sizeof(double));
+  T* rowsum = reinterpret_cast<T*>(smem + off);
+  off += align16((size_t)p.tr * sizeof(T));
   T* arow = reinterpret_cast<T*>(smem + off);
   off += align16((size_t)p.tr * sizeof(T));
   T* bcol = reinterpret_cast<T*>(smem + off);
 
   // Alg. 2 step 1.  Every block reads the same max, so a degenerate input
   // makes every block return before the first barrier.
-  const double m = from_ordered_key(*p.xmax_key);
+  const double m = p.mode == 0 ? from_ordered_key(*p.xmax_key) : 1.0;
+  const int max_sweeps = (p.gate != nullptr && p.gate->gamma <= p.gate_tol) ? 0 : p.max_sweeps;
   if (!(m > 0.0)) {
     if (blockIdx.x == 0 && tid == 0) {
       p.stats->status = DEV_DEGENERATE;
@@ -156,55 +231,61 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T> p) {
     }
     return;
   }
-  const double half_theta = p.theta / 2.0;
   const double n_d = (double)p.n;
   const double inv_n = 1.0 / n_d;
-  const double n_sq = n_d * n_d;
-  unsigned gen = 0;
+  const double inv_n2 = inv_n * inv_n;
+  const T inv_n_t = (T)inv_n;
   int* status = &p.stats->status;
+  const T scale = (T)((p.theta / 2.0) / m);
 
-  sdsn_pass<T, true>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj, half_theta,
-                     m, 0);
-  if (!grid_sync(p.bar, nblocks, gen, p.limit_ns, status, &s_flag)) return;
+  sdsn_pass<T, TIn, MAXC, true>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj,
+                                scale, 0);
+  unsigned epoch = 1;
+  if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
 
-  auto total = [&](int buf) {
+  double g = INFINITY;
+  int k = 0;
+  while (true) {
+    const int rb = k & 1;
+    // One round trip: totals (warp 0), row partials, column partials.
     if (warp == 0) {
       double s = 0.0;
-      for (unsigned t = lane; t < nblocks; t += 32) s += __ldcg(&p.tpart[(size_t)buf * nblocks + t]);
+      for (unsigned t = lane; t < nblocks; t += 32) s += __ldcg(&p.tpart[(size_t)rb * nblocks + t]);
       s = warp_sum(s);
       if (lane == 0) s_S = s;
     }
-    __syncthreads();
-    return s_S;
-  };
-
-  double S = total(0);
-  double g = INFINITY;
-  int k = 0;
-  while (k < p.max_sweeps) {
-    const int rb = k & 1, wb = rb ^ 1;
-    const double c1 = inv_n + S / n_sq;
-    // Row sums of my rows (Q partials each) -> a_i; column sums -> b_j.
-    for (int i = tid; i < nr; i += kSdsnThreads) {
-      const double* rp = p.rpart + (size_t)rb * p.Q * p.n + r0 + i;
-      double r = 0.0;
-      for (int q = 0; q < p.Q; ++q) r += __ldcg(rp + (size_t)q * p.n);
-      arow[i] = (T)(c1 - r / n_d);
-    }
-    for (int j = tid; j < nc; j += kSdsnThreads) {
-      const double* cp = p.cpart + (size_t)rb * p.P * p.n + c0 + j;
-      double c = 0.0;
-      for (int q = 0; q < p.P; ++q) c += __ldcg(cp + (size_t)q * p.n);
-      bcol[j] = (T)(c / n_d);
+    for (int e = tid; e < nr + nc; e += kSdsnThreads) {
+      const bool is_row = e < nr;
+      const int idx = is_row ? e : e - nr;
+      const int cnt = is_row ? p.Q : p.P;
+      const T* src = is_row ? p.rpart + (size_t)rb * p.Q * p.n + r0 + idx
+                            : p.cpart + (size_t)rb * p.P * p.n + c0 + idx;
+      T v[kMaxGrid];
+#pragma unroll
+      for (int q = 0; q < kMaxGrid; ++q) v[q] = q < cnt ? __ldcg(src + (size_t)q * p.n) : T(0);
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < kMaxGrid; ++q) acc += v[q];
+      if (is_row)
+        rowsum[idx] = acc;
+      else
+        bcol[idx] = acc * inv_n_t;
     }
     __syncthreads();
-    sdsn_pass<T, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj,
-                        half_theta, m, wb);
+    const double S = s_S;
+    if (k > 0 || p.mode == 1) {
+      g = S * inv_n - 1.0;
+      if (g <= p.gamma_tol) break;
+    }
+    if (k >= max_sweeps) break;
+    const T c1 = (T)(inv_n + S * inv_n2);
+    for (int i = tid; i < nr; i += kSdsnThreads) arow[i] = c1 - rowsum[i] * inv_n_t;
+    __syncthreads();
+    sdsn_pass<T, TIn, MAXC, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi,
+                                   bj, scale, rb ^ 1);
     ++k;
-    if (!grid_sync(p.bar, nblocks, gen, p.limit_ns, status, &s_flag)) return;
-    S = total(wb);
-    g = S / n_d - 1.0;
-    if (g <= p.gamma_tol) break;
+    ++epoch;
+    if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
   }
 
   if (p.resident) {
@@ -222,47 +303,58 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T> p) {
   }
 }
 
-// Grid shape: square-ish P x Q with P*Q co-resident CTAs; a single CTA for
-// small n (no grid barrier traffic beyond its own block).
+// Grid shape: square P x Q with P*Q co-resident CTAs; a single CTA for small
+// n (its barrier is then only the block's own).
 void choose_grid(int n, int max_blocks, int& P, int& Q) {
   if (n <= 96) {
     P = Q = 1;
     return;
   }
   int g = 1;
-  while ((g + 1) * (g + 1) <= max_blocks) ++g;
+  while ((g + 1) * (g + 1) <= max_blocks && g + 1 <= kMaxGrid) ++g;
   const int lim = (n + 47) / 48;  // tiles of at least ~48 x 48
   P = Q = g < lim ? g : lim;
 }
 
-template <typename T>
+template <typename T, typename TIn, int MAXC>
+int launch_k(SdsnK<T, TIn>& k, int nblocks, size_t smem, int num_sms, cudaStream_t s) {
+  static int per_sm = -1;  // occupancy does not depend on the (capped) smem size here
+  if (per_sm < 0) {
+    if (cudaFuncSetAttribute(sdsn_kernel<T, TIn, MAXC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) !=
+        cudaSuccess)
+      return -1;
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sdsn_kernel<T, TIn, MAXC>, kSdsnThreads,
+                                                      kSmemCap) != cudaSuccess)
+      return -1;
+    per_sm = v;
+  }
+  if (per_sm < 1 || nblocks > per_sm * num_sms) return -1;
+  void* args[] = {&k};
+  if (cudaLaunchCooperativeKernel((const void*)sdsn_kernel<T, TIn, MAXC>, dim3(nblocks),
+                                  dim3(kSdsnThreads), args, smem, s) != cudaSuccess)
+    return -1;
+  return 1;
+}
+
+template <typename T, typename TIn>
 int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
-  SdsnK<T> k{};
-  k.n = L.n;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int per_sm = 0;
+  SdsnK<T, TIn> k{};
   int P, Q;
-  // Occupancy with the largest footprint we may request is at least 1/SM.
   choose_grid(L.n, num_sms, P, Q);
-  int tr = (L.n + P - 1) / P, tc = (L.n + Q - 1) / Q;
-  bool resident = sdsn_smem_bytes<T>(tr, tc, true) <= kSmemCap;
-  size_t smem = sdsn_smem_bytes<T>(tr, tc, resident);
+  const int tr = (L.n + P - 1) / P, tc = (L.n + Q - 1) / Q;
+  const bool resident = sdsn_smem_bytes<T>(tr, tc, true) <= kSmemCap;
+  const size_t smem = sdsn_smem_bytes<T>(tr, tc, resident);
   if (smem > kSmemCap) return -1;  // tile rows too long even for streaming
-  if (cudaFuncSetAttribute(sdsn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sdsn_kernel<T>, kSdsnThreads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    return -1;
-  if (P * Q > per_sm * num_sms) return -1;
+  k.n = L.n;
   k.P = P;
   k.Q = Q;
   k.tr = tr;
   k.tc = tc;
   k.resident = resident ? 1 : 0;
-  k.X = static_cast<const T*>(L.X);
+  k.mode = L.mode;
+  k.X = static_cast<const TIn*>(L.X);
   k.ldx = L.ldx;
   k.Y = static_cast<T*>(L.Y);
   k.ldy = L.ldy;
@@ -270,31 +362,38 @@ int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   k.gamma_tol = L.gamma_tol;
   k.max_sweeps = L.max_sweeps;
   k.xmax_key = L.xmax_key;
+  k.gate = L.gate;
+  k.gate_tol = L.gate_tol;
   k.stats = L.stats;
-  k.rpart = L.partials;
+  k.rpart = reinterpret_cast<T*>(L.partials);
   k.cpart = k.rpart + (size_t)2 * Q * L.n;
-  k.tpart = k.cpart + (size_t)2 * P * L.n;
+  k.tpart = L.partials + (size_t)2 * (P + Q) * L.n;  // past both partial arrays (<= 8-byte T)
   k.bar = L.barrier;
   k.limit_ns = L.limit_ns;
   if (cudaMemsetAsync(L.barrier, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
-  void* args[] = {&k};
-  if (cudaLaunchCooperativeKernel((const void*)sdsn_kernel<T>, dim3(P * Q), dim3(kSdsnThreads),
-                                  args, smem, s) != cudaSuccess)
-    return -1;
-  (void)dev;
-  return 1;
+  const int slots = (tc + 31) / 32;
+  if (slots <= 4) return launch_k<T, TIn, 4>(k, P * Q, smem, num_sms, s);
+  if (slots <= 24) return launch_k<T, TIn, 24>(k, P * Q, smem, num_sms, s);
+  return launch_k<T, TIn, 0>(k, P * Q, smem, num_sms, s);
 }
 
 }  // namespace
 
 size_t sdsn_partials_elems(int n, int max_blocks) {
   int g = 1;
-  while ((g + 1) * (g + 1) <= max_blocks) ++g;
+  while ((g + 1) * (g + 1) <= max_blocks && g + 1 <= kMaxGrid) ++g;
   return (size_t)4 * g * (size_t)n + 2 * (size_t)g * g + 64;
 }
 
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
-  return launch_sdsn_t<double>(L, num_sms, s);
+  return launch_sdsn_t<double, double>(L, num_sms, s);
+}
+
+int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
+  if (!L.in_fp32 && !L.out_fp32) return launch_sdsn_t<double, double>(L, num_sms, s);
+  if (L.in_fp32 && L.out_fp32) return launch_sdsn_t<float, float>(L, num_sms, s);
+  if (L.in_fp32 && !L.out_fp32) return launch_sdsn_t<double, float>(L, num_sms, s);
+  return -1;
 }
 
 }  // namespace fram

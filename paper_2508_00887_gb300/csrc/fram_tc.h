@@ -1,0 +1,17 @@
+// Internal launchers of the mixed-precision path (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fram {
+
+// C = A * Bop^T on ld x ld K-major operands with tcgen05 tensor cores.
+// kind: 0 = BF16 operands, 1 = TF32 (FP32 storage).  out_kind: 0 = FP32,
+// 1 = BF16, 2 = TF32-rounded FP32.  Optional lambda*K term and max(C) over
+// the leading n x n block.  err receives DEV_TIMEOUT if a wait expired.
+int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int kind, int out_kind,
+                   const double* Kmat, double lam, unsigned long long* cmax, int* err,
+                   uint64_t limit_ns, cudaStream_t s);
+
+}  // namespace fram

@@ -68,11 +68,13 @@ int main(void) {{
 
 @pytest.mark.parametrize("cname,pystruct,cfields", [
     ("fram_params", fr.FramParams,
-     ["lambda", "alpha", "theta", "delta_tol", "gamma_tol", "polish_tol", "max_outer",
+     ["lambda", "alpha", "theta", "delta_tol", "gamma_tol", "polish_tol", "stall_ratio",
+      "stall_below", "max_outer",
       "max_sweeps", "max_polish", "precision", "init", "reserved"]),
     ("fram_info", fr.FramInfo,
      ["outer_iters", "total_sweeps", "polish_sweeps", "sdsn_converged_last", "lap_augmentations",
-      "reserved", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total"]),
+      "reserved", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total",
+      "ms_gemm", "ms_sdsn", "ms_polish", "ms_update"]),
 ])
 def test_struct_layouts_match_header(cname, pystruct, cfields):
     size, offs = _c_layout(cname, cfields)
