@@ -33,6 +33,9 @@ import fram_inputs as fi  # noqa: E402
 METRIC = "FRAM solves/s and ms/solve, mixed vs FP64 on 1 GB300 at equal accuracy; p50/p99 latency"
 UNIT = "solves/s"
 
+BATCH_DESC = ("4096 keypoint-like Gaussian-kernel pairs, n ~ U{10..64}, 0-20% outliers per side "
+              "padded with dummy nodes, N(0,0.02) jitter, theta=2; one batched call per step")
+
 WORKLOADS = {
     "small": ("ER pair n=50, p=0.2, U(0,1), N(0,0.02) edge noise, theta=10", fi.small_er_pair),
     "medium": ("ER pair n=1000, p=0.05, U(0,1), N(0,0.05) noise, 5% edge flips, theta=10",
@@ -188,6 +191,102 @@ def time_solves(fr, torch, ctx, n, A, B, params, steps, warmup, flush, count_lau
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
     return ms, infos, X, P, fr.fram_kernel_launches(ctx) - launches0
+
+
+def run_batch(args):
+    """Batched workload: one step = one fram_solve_batched call (one persistent
+    kernel launch replayed from a CUDA graph) over 4096 small pairs."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2508_00887_gb300 import build
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import paper_2508_00887_gb300 as fr
+    fr.load()
+    pairs = fi.keypoint_batch(args.batch_count, seed=rank)
+    ns = [g.n for g in pairs]
+    stream = torch.cuda.current_stream()
+    ctx = fr.fram_create(dev, 0, stream.cuda_stream)
+    params = fr.fram_default_params(theta=2.0, precision=PRECISIONS[args.precision])
+    As = [torch.from_numpy(g.A).cuda() for g in pairs]
+    Bs = [torch.from_numpy(g.B).cuda() for g in pairs]
+    Ps = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = fr.fram_kernel_launches(ctx)
+    with ClockSampler(dev) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            _, infos = fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = fr.fram_kernel_launches(ctx) - l0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = ws * args.steps * len(pairs) / total_s
+    # End to end with host buffers (pinned): packing, copies and unpacking inside.
+    Ah = [torch.from_numpy(g.A).pin_memory().numpy() for g in pairs]
+    Bh = [torch.from_numpy(g.B).pin_memory().numpy() for g in pairs]
+    Ph = [np.empty(g.n, dtype=np.int32) for g in pairs]
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        fr.fram_solve_batched(ctx, ns, Ah, Bh, params, None, Ph)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if rank == 0:
+        import oracle as o
+        acc = float(np.mean([o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Ps, pairs)]))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": BATCH_DESC, "pairs": len(pairs), "precision": args.precision,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "solve": {"mean_accuracy": acc,
+                      "mean_outer_iters": float(np.mean([i.outer_iters for i in infos])),
+                      "mean_sweeps": float(np.mean([i.total_sweeps for i in infos]))},
+            "e2e": {"value": ws * len(pairs) / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(2 * g.n * g.n * 8 for g in pairs)),
+                    "d2h_bytes_per_step": int(sum(g.n * 4 for g in pairs))},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            sample = pairs[:args.cpu_pairs]
+            t0 = time.perf_counter()
+            for g in sample:
+                o.fram(g.A, g.B, theta=2.0)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": len(sample) / dt, "unit": UNIT, "cores": cpu_cores(),
+                                    "kind": "oracle",
+                                    "sample": f"numpy FP64 oracle on the first {len(sample)} pairs "
+                                              f"of the batch ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    fr.fram_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
 
 
 def run_ours(args):
@@ -363,7 +462,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="medium")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch"], default="medium")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--cpu-pairs", type=int, default=100)
     ap.add_argument("--precision", choices=list(PRECISIONS), default="bf16")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--cpu-iters", type=int, default=3)
@@ -372,6 +473,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

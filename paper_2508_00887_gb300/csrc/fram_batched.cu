@@ -1,0 +1,856 @@
+// Batched FRAM for many small pairs (n <= 64) in one persistent launch.
+//
+// Each CTA takes pairs from a work queue (one atomic per pair, pairs sorted
+// by decreasing n on the host) and runs the whole of Alg. 1 + Alg. 2 + eq. 2
+// of arXiv 2508.00887 for that pair in shared memory:
+//   validation and prescale (Sec. 3; Alg. 1 steps 2-3), N0 = 11^T/n (reading
+//   (i)), per outer iteration the two gradient products (step 5, FFMA/DFMA on
+//   64 x 64 zero-padded tiles), SDSN (Alg. 2, eq. 7), the FP64 update and
+//   delta (steps 7-8), then the Hungarian assignment (eq. 2; one warp, row
+//   argmax warm start + shortest augmenting paths with the columns' state in
+//   registers) and the objective (eq. 1, Sec. 7) on the unscaled inputs.
+// T = double is the FP64 path (same arithmetic as the single-pair FP64
+// path); T = float runs the gradient and SDSN in FP32 and keeps N, the
+// update and delta in FP64, with the mixed paths' rounding-floor stop.
+// Nothing in the kernel waits on another CTA.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fram_ctx.h"
+
+namespace fram {
+
+namespace {
+
+constexpr int NMAX = 64;
+constexpr int LDS = NMAX + 1;
+
+struct BatchDesc {
+  int n;
+  int index;           // position in the caller's arrays (host bookkeeping)
+  long long off_mat;   // element offset of the pair's n x n blocks
+  long long off_vec;   // element offset of the pair's n-vectors
+};
+
+struct BatchInfo {
+  int outer_iters, total_sweeps, status, lap_aug;
+  double delta, gamma, objective, match_error, assignment_value;
+};
+
+struct BatchArgs {
+  const BatchDesc* desc;
+  int count;
+  const double* A;
+  const double* B;
+  double* Nout;
+  int32_t* perm;
+  BatchInfo* info;
+  unsigned* queue;
+  double lam, alpha, theta, delta_tol, gamma_tol, stall_ratio, stall_below;
+  int max_outer, max_sweeps, use_stall;
+};
+
+enum : int { PAIR_OK = 0, PAIR_INVALID = 1, PAIR_DEGENERATE = 2 };
+
+template <typename T>
+__host__ __device__ constexpr size_t batched_smem_bytes(int nt) {
+  return 5 * (size_t)NMAX * LDS * sizeof(T) + (size_t)NMAX * NMAX * sizeof(double) +
+         4 * (size_t)NMAX * sizeof(T) + (size_t)(nt / 64) * NMAX * sizeof(T) +
+         (size_t)NMAX * sizeof(double) + 64 * sizeof(double);
+}
+
+// Block reductions over NT threads; result broadcast to all threads.
+template <int NT>
+__device__ __forceinline__ double bsum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) r += red[w];
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double bmax(double v, double* red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = -INFINITY;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) r = fmax(r, red[w]);
+  return r;
+}
+
+__device__ __forceinline__ double relu_d(double y) {
+  const long long b = __double_as_longlong(y);
+  return __longlong_as_double(b & ~(b >> 63));
+}
+__device__ __forceinline__ float relu_d(float y) {
+  const int b = __float_as_int(y);
+  return __int_as_float(b & ~(b >> 31));
+}
+
+// C[i][j] = sum_{k<n} Aop[i][k] * Bop[k][j] over the 64 x 64 padded tile.
+// Returns the thread's max over i, j < n when want_max.
+template <typename T, int NT>
+__device__ __forceinline__ T small_gemm(const T* __restrict__ Aop, const T* __restrict__ Bop,
+                                        T* __restrict__ C, int n, bool want_max) {
+  constexpr int RY = NT / 16;        // rows per step
+  constexpr int RA = NMAX / RY;      // row repeats
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[RA][4];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k = 0; k < n; ++k) {
+    T av[RA], bv[4];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) av[a] = Aop[(ty + RY * a) * LDS + k];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bop[k * LDS + tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+  T mx = T(-INFINITY);
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ty + RY * a, j = tx + 16 * b;
+      C[i * LDS + j] = acc[a][b];
+      if (want_max && i < n && j < n) mx = acc[a][b] > mx ? acc[a][b] : mx;
+    }
+  return mx;
+}
+
+// One pass of SDSN on Ys (n x n): FIRST scales by `scale`; otherwise the fused
+// P1+P2 sweep with arow/bcol.  Leaves row sums in rs, column sums in cs and
+// returns S (FP64) to every thread.
+template <typename T, int NT, bool FIRST>
+__device__ __forceinline__ double small_sdsn_pass(T* Ys, T* rs, T* cs, const T* arow,
+                                                  const T* bcol, T* cpart, double* red, int n,
+                                                  T scale) {
+  constexpr int G = NT / 64;  // row groups
+  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
+  if (c < n) {
+    T acc = T(0);
+    const T bc = FIRST ? T(0) : bcol[c];
+    for (int r = rg; r < n; r += G) {
+      T y = Ys[r * LDS + c];
+      y = FIRST ? y * scale : relu_d((y + arow[r]) - bc);
+      Ys[r * LDS + c] = y;
+      acc += y;
+    }
+    cpart[rg * NMAX + c] = acc;
+  }
+  __syncthreads();
+  {
+    const int r = tid / G, part = tid % G;  // G consecutive lanes per row
+    T s = T(0);
+    if (r < n)
+      for (int j = part; j < n; j += G) s += Ys[r * LDS + j];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (part == 0 && r < n) rs[r] = s;
+  }
+  if (tid < n) {
+    T s = T(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) s += cpart[g * NMAX + tid];
+    cs[tid] = s;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double s = 0.0;
+    if (tid < n) s += (double)rs[tid];
+    if (tid + 32 < n) s += (double)rs[tid + 32];
+    s = warp_sum(s);
+    if (tid == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Warp 0: Hungarian on W (n x n, row stride NMAX) for maximum sum.  Lane l
+// owns columns l and l + 32; row potentials live in shared memory.
+__device__ void small_lap(const double* W, int n, double* u, int* rowcol, int* argc,
+                          double* rowmax, int* aug_out) {
+  const int lane = threadIdx.x & 31;
+  // Row argmax (ties -> lowest column).
+  for (int i = 0; i < n; ++i) {
+    double best = -INFINITY;
+    int bj = 0x7fffffff;
+    for (int j = lane; j < n; j += 32) {
+      const double x = W[i * NMAX + j];
+      if (x > best) { best = x; bj = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+    }
+    if (lane == 0) {
+      argc[i] = bj;
+      rowmax[i] = best;
+    }
+  }
+  __syncwarp();
+  // Column state in registers: slot s <-> column lane + 32 s.
+  int colrow[2] = {-1, -1};
+  double v[2] = {0.0, 0.0};
+  for (int i = 0; i < n; ++i) {  // lowest row claiming a column keeps it
+    const int j = argc[i];
+    if ((j & 31) == lane && colrow[j >> 5] == -1) colrow[j >> 5] = i;
+  }
+  for (int i = lane; i < n; i += 32) u[i] = -rowmax[i];
+  __syncwarp();
+  for (int i = 0; i < n; ++i) {
+    const int j = argc[i];
+    const int owner = __shfl_sync(0xffffffffu, colrow[(j >> 5) & 1], j & 31);
+    if (lane == 0) rowcol[i] = owner == i ? j : -1;
+  }
+  __syncwarp();
+  int aug = 0;
+  for (int root = 0; root < n; ++root) {
+    if (rowcol[root] != -1) continue;
+    ++aug;
+    double minv[2] = {INFINITY, INFINITY};
+    int used[2] = {0, 0}, way[2] = {-1, -1};
+    int i0 = root, j0 = -1, j1 = -1;
+    for (int step = 0; step <= n; ++step) {
+      const double ui = u[i0];
+      double best = INFINITY;
+      int bj = 0x7fffffff;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int j = lane + 32 * s;
+        if (j < n && !used[s]) {
+          const double cur = -W[i0 * NMAX + j] - ui - v[s];
+          if (cur < minv[s]) { minv[s] = cur; way[s] = j0; }
+          if (minv[s] < best) { best = minv[s]; bj = j; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+      }
+      const double delta = best;
+      j1 = bj;
+      __syncwarp();
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int j = lane + 32 * s;
+        if (j < n) {
+          if (used[s]) {
+            v[s] -= delta;
+            u[colrow[s]] += delta;
+          } else {
+            minv[s] -= delta;
+          }
+        }
+      }
+      if (lane == 0) u[root] += delta;
+      if ((j1 & 31) == lane) used[j1 >> 5] = 1;
+      __syncwarp();
+      j0 = j1;
+      const int nxt = __shfl_sync(0xffffffffu, colrow[(j1 >> 5) & 1], j1 & 31);
+      if (nxt == -1) break;
+      i0 = nxt;
+    }
+    // Augment along the predecessor chain.
+    int j = j1;
+    while (j != -1) {
+      const int jp = __shfl_sync(0xffffffffu, way[(j >> 5) & 1], j & 31);
+      const int r = jp == -1 ? root : __shfl_sync(0xffffffffu, colrow[(jp >> 5) & 1], jp & 31);
+      if ((j & 31) == lane) colrow[j >> 5] = r;
+      if (lane == 0) rowcol[r] = j;
+      j = jp;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) *aug_out = aug;
+  __syncwarp();
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* As = reinterpret_cast<T*>(smem);
+  T* Bs = As + NMAX * LDS;
+  T* Nc = Bs + NMAX * LDS;
+  T* Ts = Nc + NMAX * LDS;
+  T* Ys = Ts + NMAX * LDS;
+  double* N64 = reinterpret_cast<double*>(Ys + NMAX * LDS);
+  T* rs = reinterpret_cast<T*>(N64 + NMAX * NMAX);
+  T* cs = rs + NMAX;
+  T* arow = cs + NMAX;
+  T* bcol = arow + NMAX;
+  T* cpart = bcol + NMAX;
+  double* u = reinterpret_cast<double*>(cpart + (NT / 64) * NMAX);
+  double* red = u + NMAX;  // [0,32) reductions, [32] broadcast slot
+  __shared__ int s_pair, s_aug;
+  __shared__ int rowcol[NMAX], argc[NMAX];
+  __shared__ double rowmax[NMAX];
+  const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
+  constexpr int G = NT / 64;
+
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_pair = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int pi = s_pair;
+    if (pi >= a.count) break;
+    const BatchDesc d = a.desc[pi];
+    const int n = d.n;
+    const double* Ag = a.A + d.off_mat;
+    const double* Bg = a.B + d.off_mat;
+    BatchInfo info{};
+
+    // Validation (Sec. 3 graph model, reading (vii)) and max for the prescale.
+    double mA = 0.0, mB = 0.0, asA = 0.0, asB = 0.0, bad = 0.0;
+    for (int e = tid; e < n * n; e += NT) {
+      const int i = e / n, j = e - i * n;
+      const double x = Ag[e], y = Bg[e];
+      if (!isfinite(x) || x < 0.0 || !isfinite(y) || y < 0.0) {
+        bad = 1.0;
+        continue;
+      }
+      mA = fmax(mA, x);
+      mB = fmax(mB, y);
+      const double xt = Ag[j * n + i], yt = Bg[j * n + i];
+      if (isfinite(xt)) asA = fmax(asA, fabs(x - xt));
+      if (isfinite(yt)) asB = fmax(asB, fabs(y - yt));
+    }
+    bad = bmax<NT>(bad, red);
+    mA = bmax<NT>(mA, red);
+    mB = bmax<NT>(mB, red);
+    asA = bmax<NT>(asA, red);
+    asB = bmax<NT>(asB, red);
+    const double cc = fmax(mA, mB);
+    if (bad > 0.0 || asA > 1e-12 * fmax(mA, 1.0) || asB > 1e-12 * fmax(mB, 1.0)) {
+      info.status = PAIR_INVALID;
+    } else if (!(cc > 0.0)) {
+      info.status = PAIR_DEGENERATE;
+    }
+    if (info.status != PAIR_OK) {
+      if (tid == 0) a.info[pi] = info;
+      continue;
+    }
+    // Alg. 1 steps 2-3 and the initial N (reading (i)), zero-padded tiles.
+    const double sq = sqrt(cc);
+    const double n0 = 1.0 / n;
+    for (int e = tid; e < NMAX * NMAX; e += NT) {
+      const int i = e >> 6, j = e & 63;
+      const bool in = i < n && j < n;
+      As[i * LDS + j] = in ? (T)(Ag[i * n + j] / sq) : T(0);
+      Bs[i * LDS + j] = in ? (T)(Bg[i * n + j] / sq) : T(0);
+      Nc[i * LDS + j] = in ? (T)n0 : T(0);
+      N64[i * NMAX + j] = in ? n0 : 0.0;
+    }
+    __syncthreads();
+
+    const double inv_n = 1.0 / n, inv_n2 = inv_n * inv_n;
+    const T inv_n_t = (T)inv_n;
+    const double gtol = a.gamma_tol;
+    double prev_delta = INFINITY, delta = INFINITY, g = INFINITY;
+    int t = 0, sweeps_total = 0;
+    while (t < a.max_outer) {
+      // Step 5: T = A N, X = T B.
+      small_gemm<T, NT>(As, Nc, Ts, n, false);
+      __syncthreads();
+      const T lm = small_gemm<T, NT>(Ts, Bs, Ys, n, true);
+      const double m = bmax<NT>((double)lm, red);
+      if (!(m > 0.0)) {
+        info.status = PAIR_DEGENERATE;
+        break;
+      }
+      // Step 6: SDSN.
+      double S = small_sdsn_pass<T, NT, true>(Ys, rs, cs, arow, bcol, cpart, red, n,
+                                              (T)((a.theta / 2.0) / m));
+      int k = 0;
+      while (true) {
+        if (k > 0) {
+          g = S * inv_n - 1.0;
+          if (g <= gtol) break;
+        }
+        if (k >= a.max_sweeps) break;
+        const T c1 = (T)(inv_n + S * inv_n2);
+        if (tid < n) {
+          arow[tid] = c1 - rs[tid] * inv_n_t;
+          bcol[tid] = cs[tid] * inv_n_t;
+        }
+        __syncthreads();
+        S = small_sdsn_pass<T, NT, false>(Ys, rs, cs, arow, bcol, cpart, red, n, T(1));
+        ++k;
+      }
+      sweeps_total += k;
+      // Steps 7-8 in FP64.
+      double d2 = 0.0, nn2 = 0.0;
+      if (c < n)
+        for (int r = rg; r < n; r += G) {
+          const double old = N64[r * NMAX + c];
+          const double nn = __dadd_rn(__dmul_rn(1.0 - a.alpha, old),
+                                      __dmul_rn(a.alpha, (double)Ys[r * LDS + c]));
+          const double dd = __dsub_rn(nn, old);
+          N64[r * NMAX + c] = nn;
+          Nc[r * LDS + c] = (T)nn;
+          d2 = fma(dd, dd, d2);
+          nn2 = fma(nn, nn, nn2);
+        }
+      d2 = bsum<NT>(d2, red);
+      nn2 = bsum<NT>(nn2, red);
+      delta = sqrt(d2) / sqrt(nn2);
+      ++t;
+      if (delta <= a.delta_tol) break;
+      if (a.use_stall && a.stall_ratio > 0.0 && delta <= a.stall_below &&
+          delta > a.stall_ratio * prev_delta)
+        break;
+      prev_delta = delta;
+    }
+    __syncthreads();
+    if (info.status != PAIR_OK) {
+      if (tid == 0) a.info[pi] = info;
+      continue;
+    }
+    // Step 10 (eq. 2): warp 0.
+    if (tid < 32) small_lap(N64, n, u, rowcol, argc, rowmax, &s_aug);
+    __syncthreads();
+    // Objective (eq. 1) and matching error (Sec. 7) on the unscaled inputs.
+    double s1 = 0.0, s2 = 0.0;
+    for (int e = tid; e < n * n; e += NT) {
+      const int i = e / n, j = e - i * n;
+      const double x = Ag[e];
+      const double y = Bg[rowcol[i] * n + rowcol[j]];
+      s1 = fma(x, y, s1);
+      s2 = fma(x - y, x - y, s2);
+    }
+    double av = 0.0;
+    if (tid < n) av = N64[tid * NMAX + rowcol[tid]];
+    s1 = bsum<NT>(s1, red);
+    s2 = bsum<NT>(s2, red);
+    av = bsum<NT>(av, red);
+    int32_t* pout = a.perm + d.off_vec;
+    for (int i = tid; i < n; i += NT) pout[i] = rowcol[i];
+    if (a.Nout != nullptr) {
+      double* no = a.Nout + d.off_mat;
+      for (int e = tid; e < n * n; e += NT) {
+        const int i = e / n, j = e - i * n;
+        no[e] = N64[i * NMAX + j];
+      }
+    }
+    if (tid == 0) {
+      info.outer_iters = t;
+      info.total_sweeps = sweeps_total;
+      info.delta = delta;
+      info.gamma = g;
+      info.objective = 0.5 * s1;
+      info.match_error = 0.5 * sqrt(s2);
+      info.assignment_value = av;
+      info.lap_aug = s_aug;
+      a.info[pi] = info;
+    }
+  }
+}
+
+// Gather caller matrices (device pointers, table by processing position)
+// into the packed input buffers.
+__global__ void gather_kernel(const double* const* srcA, const double* const* srcB,
+                              const BatchDesc* desc, int count, double* A, double* B) {
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const BatchDesc d = desc[p];
+    const double* sa = srcA[p];
+    const double* sb = srcB[p];
+    for (int e = threadIdx.x; e < d.n * d.n; e += blockDim.x) {
+      A[d.off_mat + e] = sa[e];
+      B[d.off_mat + e] = sb[e];
+    }
+  }
+}
+
+// Scatter packed outputs to caller device buffers.
+__global__ void scatter_kernel(const BatchDesc* desc, int count, const double* Nout,
+                               const int32_t* perm, double* const* dstX, int32_t* const* dstP) {
+  for (int p = blockIdx.x; p < count; p += gridDim.x) {
+    const BatchDesc d = desc[p];
+    if (dstX != nullptr && dstX[p] != nullptr)
+      for (int e = threadIdx.x; e < d.n * d.n; e += blockDim.x) dstX[p][e] = Nout[d.off_mat + e];
+    for (int i = threadIdx.x; i < d.n; i += blockDim.x) dstP[p][i] = perm[d.off_vec + i];
+  }
+}
+
+// Device state of the batched path, grown on demand.
+struct BatchedState {
+  size_t cap_mat = 0, cap_vec = 0, cap_count = 0;
+  double *A = nullptr, *B = nullptr, *N = nullptr;
+  int32_t* perm = nullptr;
+  BatchDesc* desc = nullptr;
+  BatchInfo* info = nullptr;
+  void** ptrs = nullptr;        // device tables by position: A, B, X, perm (4 x count)
+  unsigned* queue = nullptr;
+  size_t hcap_mat = 0, hcap_vec = 0, hcap_count = 0;
+  double *hA = nullptr, *hB = nullptr, *hN = nullptr;
+  int32_t* hperm = nullptr;
+  BatchDesc* hdesc = nullptr;
+  BatchInfo* hinfo = nullptr;
+  void** hptrs = nullptr;
+  int tuned_nt[2] = {0, 0};     // autotuned block size per precision (0 = not tuned)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  // signature of the captured graph
+  int g_nt = 0, g_scatter = -1;
+  void* g_ptrs = nullptr;
+  BatchArgs g_args{};
+};
+
+template <typename T>
+void set_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(batched_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batched_smem_bytes<T>(128));
+  cudaFuncSetAttribute(batched_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batched_smem_bytes<T>(256));
+  cudaFuncSetAttribute(batched_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batched_smem_bytes<T>(512));
+  done = true;
+}
+
+template <typename T>
+int launch_batched(const BatchArgs& a, int nt, int num_sms, cudaStream_t s) {
+  set_attrs<T>();
+  int grid = num_sms < a.count ? num_sms : a.count;
+  if (grid < 1) grid = 1;
+  switch (nt) {
+    case 128:
+      batched_kernel<T, 128><<<grid, 128, batched_smem_bytes<T>(128), s>>>(a);
+      break;
+    case 256:
+      batched_kernel<T, 256><<<grid, 256, batched_smem_bytes<T>(256), s>>>(a);
+      break;
+    default:
+      batched_kernel<T, 512><<<grid, 512, batched_smem_bytes<T>(512), s>>>(a);
+      break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_batched_any(bool fp32, const BatchArgs& a, int nt, int num_sms, cudaStream_t s) {
+  return fp32 ? launch_batched<float>(a, nt, num_sms, s)
+              : launch_batched<double>(a, nt, num_sms, s);
+}
+
+// Grow a device (pinned host when host == true) buffer to `need` elements.
+template <typename P>
+bool grow(P** ptr, size_t& cap, size_t need, bool host = false) {
+  if (need <= cap && *ptr) return true;
+  if (*ptr) host ? cudaFreeHost(*ptr) : cudaFree(*ptr);
+  *ptr = nullptr;
+  cap = 0;
+  const size_t bytes = (need ? need : 1) * sizeof(P);
+  cudaError_t e = host ? cudaMallocHost(reinterpret_cast<void**>(ptr), bytes)
+                       : cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return false;
+  }
+  cap = need;
+  return true;
+}
+
+}  // namespace
+
+void batched_release(fram_ctx* c) {
+  BatchedState* b = static_cast<BatchedState*>(c->batched);
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  void* dptr[] = {b->A, b->B, b->N, b->perm, b->desc, b->info, b->ptrs, b->queue};
+  for (void* p : dptr)
+    if (p) cudaFree(p);
+  void* hptr[] = {b->hA, b->hB, b->hN, b->hperm, b->hdesc, b->hinfo, b->hptrs};
+  for (void* p : hptr)
+    if (p) cudaFreeHost(p);
+  delete b;
+  c->batched = nullptr;
+}
+
+// Solve the pairs `idx` (all with n <= 64) of one fram_solve_batched call in
+// one persistent launch.  Inputs and outputs must each be all-host or
+// all-device.
+fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const int* n,
+                              const double* const* A, const double* const* B,
+                              const fram_params& p, double* const* X_out,
+                              int32_t* const* perm_out, fram_info* infos) {
+  if (!c->batched) c->batched = new BatchedState();
+  BatchedState& S = *static_cast<BatchedState*>(c->batched);
+  const int count = (int)idx.size();
+  if (count == 0) return FRAM_OK;
+  const bool fp32 = p.precision != FRAM_PREC_FP64;
+  const bool wantX = X_out != nullptr;
+  std::vector<int> order(idx);  // longest pairs first for the work queue
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return n[x] > n[y]; });
+  std::vector<BatchDesc> desc(count);
+  size_t mat = 0, vec = 0;
+  int in_dev = 0, out_dev = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = order[k];
+    desc[k] = BatchDesc{n[i], i, (long long)mat, (long long)vec};
+    mat += (size_t)n[i] * n[i];
+    vec += (size_t)n[i];
+    in_dev += (is_device_ptr(A[i]) ? 1 : 0) + (is_device_ptr(B[i]) ? 1 : 0);
+    const bool xd = !wantX || X_out[i] == nullptr || is_device_ptr(X_out[i]);
+    const bool xh = !wantX || X_out[i] == nullptr || !is_device_ptr(X_out[i]);
+    const bool pd = is_device_ptr(perm_out[i]);
+    out_dev += (pd && xd) ? 1 : ((!pd && xh) ? 0 : -count - 1);
+  }
+  if (in_dev != 0 && in_dev != 2 * count) {
+    set_err(c, "fram_solve_batched: inputs must be all host or all device buffers");
+    return FRAM_ERR_INVALID;
+  }
+  if (out_dev != 0 && out_dev != count) {
+    set_err(c, "fram_solve_batched: outputs must be all host or all device buffers");
+    return FRAM_ERR_INVALID;
+  }
+  const bool dev_in = in_dev != 0, dev_out = out_dev != 0;
+  const size_t need_bytes = 3 * mat * 8 + vec * 4 +
+                            (size_t)count * (sizeof(BatchDesc) + sizeof(BatchInfo) + 32);
+  if (c->budget && c->ws.bytes + need_bytes + c->serve_bytes > c->budget) {
+    set_err(c, "batched buffers (%zu bytes) exceed the HBM budget", need_bytes);
+    return FRAM_ERR_OOM;
+  }
+  bool ok = true;
+  size_t cm = S.cap_mat, cv = S.cap_vec, cc = S.cap_count;
+  ok = ok && grow(&S.A, cm = S.cap_mat, mat) && grow(&S.B, cm = S.cap_mat, mat) &&
+       grow(&S.N, S.cap_mat, mat);
+  ok = ok && grow(&S.perm, cv, vec);
+  ok = ok && grow(&S.desc, cc = S.cap_count, (size_t)count) &&
+       grow(&S.info, cc = S.cap_count, (size_t)count) &&
+       grow(&S.ptrs, S.cap_count, (size_t)4 * count);
+  ok = ok && (S.queue || cudaMalloc(&S.queue, 256) == cudaSuccess);
+  S.cap_vec = cv;
+  size_t hm = S.hcap_mat, hc = S.hcap_count;
+  ok = ok && grow(&S.hA, hm = S.hcap_mat, mat, true) && grow(&S.hB, hm = S.hcap_mat, mat, true) &&
+       grow(&S.hN, S.hcap_mat, mat, true);
+  ok = ok && grow(&S.hperm, S.hcap_vec, vec, true);
+  ok = ok && grow(&S.hdesc, hc = S.hcap_count, (size_t)count, true) &&
+       grow(&S.hinfo, hc = S.hcap_count, (size_t)count, true) &&
+       grow(&S.hptrs, S.hcap_count, (size_t)4 * count, true);
+  (void)cm;
+  (void)cc;
+  (void)hm;
+  (void)hc;
+  if (!ok) {
+    batched_release(c);
+    set_err(c, "batched buffers: allocation failed");
+    return FRAM_ERR_OOM;
+  }
+  cudaStream_t s = c->stream;
+#define BT_CUDA(x, what)                                   \
+  do {                                                     \
+    cudaError_t _e = (x);                                  \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, what);  \
+  } while (0)
+  memcpy(S.hdesc, desc.data(), count * sizeof(BatchDesc));
+  for (int k = 0; k < count; ++k) {
+    const int i = desc[k].index;
+    S.hptrs[k] = const_cast<double*>(A[i]);
+    S.hptrs[count + k] = const_cast<double*>(B[i]);
+    S.hptrs[2 * count + k] = wantX ? X_out[i] : nullptr;
+    S.hptrs[3 * count + k] = perm_out[i];
+  }
+  BT_CUDA(cudaMemcpyAsync(S.desc, S.hdesc, count * sizeof(BatchDesc), cudaMemcpyHostToDevice, s),
+          "copy descriptors");
+  BT_CUDA(cudaMemcpyAsync(S.ptrs, S.hptrs, 4 * count * sizeof(void*), cudaMemcpyHostToDevice, s),
+          "copy pointer tables");
+  if (dev_in) {
+    gather_kernel<<<std::min(count, 2 * c->num_sms), 256, 0, s>>>(
+        reinterpret_cast<const double* const*>(S.ptrs),
+        reinterpret_cast<const double* const*>(S.ptrs + count), S.desc, count, S.A, S.B);
+    if (cudaPeekAtLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "gather");
+    c->launches += 1;
+  } else {
+    for (int k = 0; k < count; ++k) {
+      const BatchDesc& d = desc[k];
+      memcpy(S.hA + d.off_mat, A[d.index], (size_t)d.n * d.n * 8);
+      memcpy(S.hB + d.off_mat, B[d.index], (size_t)d.n * d.n * 8);
+    }
+    BT_CUDA(cudaMemcpyAsync(S.A, S.hA, mat * 8, cudaMemcpyHostToDevice, s), "copy inputs");
+    BT_CUDA(cudaMemcpyAsync(S.B, S.hB, mat * 8, cudaMemcpyHostToDevice, s), "copy inputs");
+  }
+  BatchArgs a{};
+  a.desc = S.desc;
+  a.count = count;
+  a.A = S.A;
+  a.B = S.B;
+  a.Nout = wantX ? S.N : nullptr;
+  a.perm = S.perm;
+  a.info = S.info;
+  a.queue = S.queue;
+  a.lam = p.lambda;
+  a.alpha = p.alpha;
+  a.theta = p.theta;
+  a.delta_tol = p.delta_tol;
+  a.gamma_tol = fp32 ? std::max(p.polish_tol, p.gamma_tol) : p.gamma_tol;
+  a.stall_ratio = p.stall_ratio;
+  a.stall_below = p.stall_below;
+  a.max_outer = p.max_outer;
+  a.max_sweeps = p.max_sweeps;
+  a.use_stall = fp32 ? 1 : 0;
+
+  // Autotuner: on the first batched call per precision, time each block size
+  // on a prefix of the batch (two waves of CTAs) and keep the fastest.
+  int& nt = S.tuned_nt[fp32 ? 1 : 0];
+  if (nt == 0) {
+    float best = 1e30f;
+    BatchArgs t = a;
+    t.count = std::min(count, 2 * c->num_sms);
+    for (int cand : {128, 256, 512}) {
+      BT_CUDA(cudaMemsetAsync(S.queue, 0, 4, s), "memset");
+      BT_CUDA(cudaEventRecord(c->ev0, s), "event");
+      if (launch_batched_any(fp32, t, cand, c->num_sms, s) < 0)
+        return cuda_fail(c, cudaGetLastError(), "batched kernel");
+      BT_CUDA(cudaEventRecord(c->ev1, s), "event");
+      BT_CUDA(cudaEventSynchronize(c->ev1), "synchronize");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      c->launches += 1;
+      if (ms < best) {
+        best = ms;
+        nt = cand;
+      }
+    }
+  }
+  // Queue reset + persistent kernel (+ scatter to device outputs), captured
+  // into a CUDA graph once per configuration and replayed; the data of each
+  // call lives in device buffers the graph reads.
+  const bool scatter = dev_out;
+  const bool same = S.graph && S.g_nt == nt && S.g_scatter == (int)scatter &&
+                    S.g_ptrs == (void*)S.ptrs && memcmp(&S.g_args, &a, sizeof a) == 0;
+  if (!same) {
+    if (S.graph) cudaGraphExecDestroy(S.graph);
+    S.graph = nullptr;
+    if (!S.cap_stream &&
+        cudaStreamCreateWithFlags(&S.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_fail(c, cudaGetLastError(), "capture stream");
+    cudaGraph_t g = nullptr;
+    BT_CUDA(cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal),
+            "begin capture");
+    cudaMemsetAsync(S.queue, 0, 4, S.cap_stream);
+    launch_batched_any(fp32, a, nt, c->num_sms, S.cap_stream);
+    if (scatter)
+      scatter_kernel<<<std::min(count, 2 * c->num_sms), 256, 0, S.cap_stream>>>(
+          S.desc, count, S.N, S.perm,
+          wantX ? reinterpret_cast<double* const*>(S.ptrs + 2 * count) : nullptr,
+          reinterpret_cast<int32_t* const*>(S.ptrs + 3 * count));
+    cudaError_t ce = cudaStreamEndCapture(S.cap_stream, &g);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "end capture");
+    ce = cudaGraphInstantiate(&S.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      S.graph = nullptr;
+      return cuda_fail(c, ce, "graph instantiate");
+    }
+    S.g_nt = nt;
+    S.g_scatter = scatter;
+    S.g_ptrs = S.ptrs;
+    S.g_args = a;
+  }
+  BT_CUDA(cudaGraphLaunch(S.graph, s), "graph launch");
+  c->launches += scatter ? 2 : 1;
+  if (!scatter) {
+    if (wantX) BT_CUDA(cudaMemcpyAsync(S.hN, S.N, mat * 8, cudaMemcpyDeviceToHost, s), "copy N");
+    BT_CUDA(cudaMemcpyAsync(S.hperm, S.perm, vec * 4, cudaMemcpyDeviceToHost, s), "copy perm");
+  }
+  BT_CUDA(cudaMemcpyAsync(S.hinfo, S.info, count * sizeof(BatchInfo), cudaMemcpyDeviceToHost, s),
+          "copy info");
+  BT_CUDA(cudaStreamSynchronize(s), "synchronize");
+  fram_status worst = FRAM_OK;
+  for (int k = 0; k < count; ++k) {
+    const BatchDesc& d = desc[k];
+    const BatchInfo& bi = S.hinfo[k];
+    if (!scatter) {
+      memcpy(perm_out[d.index], S.hperm + d.off_vec, (size_t)d.n * 4);
+      if (wantX && X_out[d.index])
+        memcpy(X_out[d.index], S.hN + d.off_mat, (size_t)d.n * d.n * 8);
+    }
+    if (infos) {
+      fram_info& f = infos[d.index];
+      memset(&f, 0, sizeof f);
+      f.outer_iters = bi.outer_iters;
+      f.total_sweeps = bi.total_sweeps;
+      f.lap_augmentations = bi.lap_aug;
+      f.delta = bi.delta;
+      f.gamma = bi.gamma;
+      f.sdsn_converged_last = bi.gamma <= a.gamma_tol ? 1 : 0;
+      f.objective = bi.objective;
+      f.match_error = bi.match_error;
+      f.assignment_value = bi.assignment_value;
+    }
+    if (bi.status == PAIR_INVALID && worst == FRAM_OK) {
+      set_err(c, "fram_solve_batched: pair %d is outside the graph model", d.index);
+      worst = FRAM_ERR_INVALID;
+    } else if (bi.status == PAIR_DEGENERATE && worst == FRAM_OK) {
+      set_err(c, "fram_solve_batched: pair %d is degenerate (max(X) <= 0)", d.index);
+      worst = FRAM_ERR_DEGENERATE;
+    }
+  }
+  return worst;
+}
+
+}  // namespace fram
+
+extern "C" fram_status fram_solve_batched(fram_ctx* c, int count, const int* n,
+                                          const double* const* A, const double* const* B,
+                                          const fram_params* params, double* const* X_out,
+                                          int32_t* const* perm_out, fram_info* infos) {
+  using namespace fram;
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (count < 0 || (count > 0 && (!n || !A || !B || !perm_out))) {
+    set_err(c, "fram_solve_batched: count >= 0 and non-NULL n, A, B, perm_out are required");
+    return FRAM_ERR_INVALID;
+  }
+  fram_params p;
+  if (params)
+    p = *params;
+  else
+    fram_default_params(&p);
+  {
+    fram_status st = check_params(c, p);
+    if (st != FRAM_OK) return st;
+  }
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || !A[i] || !B[i] || !perm_out[i]) {
+      set_err(c, "fram_solve_batched: pair %d needs n >= 1 and non-NULL A, B, perm_out", i);
+      return FRAM_ERR_INVALID;
+    }
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "set device");
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<int> small;
+  for (int i = 0; i < count; ++i)
+    if (n[i] <= NMAX) small.push_back(i);
+  fram_status st = solve_small_batch(c, small, n, A, B, p, X_out, perm_out, infos);
+  if (st != FRAM_OK) return st;
+  for (int i = 0; i < count; ++i)
+    if (n[i] > NMAX) {
+      st = solve_one(c, n[i], A[i], B[i], nullptr, p, X_out ? X_out[i] : nullptr, perm_out[i],
+                     infos ? &infos[i] : nullptr);
+      if (st != FRAM_OK) return st;
+    }
+  return FRAM_OK;
+}

@@ -1,0 +1,167 @@
+"""Batched path (one persistent launch for pairs with n <= 64) through the C
+ABI: FP64 against the oracle at parity, against solo fram_solve results, and
+the FP32 mixed form at equal accuracy."""
+import numpy as np
+import pytest
+
+import fram_inputs as fi
+import oracle as o
+import paper_2508_00887_gb300 as fr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2508_00887_gb300 import build
+    build.build()
+    fr.load()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    c = fr.fram_create(0, 0, torch_cuda.cuda.current_stream().cuda_stream)
+    yield c
+    fr.fram_destroy(c)
+
+
+def relF(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def check_assignment(p, ref_perm, N_ref, g, inf=None, ref=None):
+    """The LAP optimum value is unique; the permutation is unique only without
+    (near-)ties -- padded dummy nodes give rows of N that are equal up to
+    rounding.  Compare the value on the oracle's N, require a valid
+    permutation, and require the identical permutation when the pair has no
+    dummy/isolated nodes."""
+    n = len(ref_perm)
+    assert sorted(p.tolist()) == list(range(n))
+    v_gpu = N_ref[np.arange(n), p].sum()
+    v_ref = N_ref[np.arange(n), ref_perm].sum()
+    assert abs(v_gpu - v_ref) <= 1e-12 * n
+    isolated = (g.A.sum(1) == 0).any() or (g.B.sum(1) == 0).any()
+    if not isolated:
+        assert np.array_equal(p, ref_perm), g.meta
+    if inf is not None:
+        assert abs(inf.objective - o.objective(g.A, g.B, p)) <= 1e-12 * max(1.0, abs(inf.objective))
+        if ref is not None and np.array_equal(p, ref_perm):
+            assert abs(inf.objective - ref.objective) <= 1e-12 * max(1.0, abs(ref.objective))
+            assert abs(inf.match_error - ref.match_error) <= 1e-10 * max(1.0, ref.match_error)
+
+
+def mixed_batch(seed=0):
+    """Keypoint pairs (n 10..64 with outliers), small ER pairs, and tiny n."""
+    pairs = fi.keypoint_batch(14, seed=seed)
+    pairs += [fi.er_pair(n, 1.0 if n <= 3 else 0.4, noise=0.02, seed=seed + n, theta=10.0)
+              for n in (2, 3, 7, 33, 64)]
+    pairs += [fi.small_er_pair(seed)]   # n = 50
+    return pairs
+
+
+def run_batched(torch, ctx, pairs, params, device=True, want_x=True):
+    ns = [g.n for g in pairs]
+    if device:
+        As = [torch.from_numpy(g.A).cuda() for g in pairs]
+        Bs = [torch.from_numpy(g.B).cuda() for g in pairs]
+        Xs = [torch.empty((g.n, g.n), dtype=torch.float64, device="cuda") for g in pairs]
+        Ps = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    else:
+        As = [g.A for g in pairs]
+        Bs = [g.B for g in pairs]
+        Xs = [np.empty((g.n, g.n)) for g in pairs]
+        Ps = [np.empty(g.n, dtype=np.int32) for g in pairs]
+    st, infos = fr.fram_solve_batched(ctx, ns, As, Bs, params, Xs if want_x else None, Ps)
+    conv = (lambda t: t.cpu().numpy()) if device else (lambda t: t)
+    return [conv(x) for x in Xs], [conv(p).astype(np.int64) for p in Ps], infos
+
+
+def test_batched_fp64_matches_oracle(torch_cuda, ctx):
+    pairs = mixed_batch(0)
+    X, P, infos = run_batched(torch_cuda, ctx, pairs, None)
+    for g, x, p, inf in zip(pairs, X, P, infos):
+        ref = o.fram(g.A, g.B, theta=10.0)
+        assert inf.outer_iters == ref.outer_iters
+        assert relF(x, ref.N) <= 1e-9, g.meta
+        check_assignment(p, ref.perm, ref.N, g, inf, ref)
+
+
+def test_batched_equals_solo(torch_cuda, ctx):
+    torch = torch_cuda
+    pairs = mixed_batch(1)
+    params = fr.fram_default_params(theta=2.0)
+    X, P, infos = run_batched(torch, ctx, pairs, params)
+    for g, x, p, inf in zip(pairs, X, P, infos):
+        Xs = torch.empty((g.n, g.n), dtype=torch.float64, device="cuda")
+        Ps = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        _, si = fr.fram_solve(ctx, g.n, torch.from_numpy(g.A).cuda(), torch.from_numpy(g.B).cuda(),
+                              None, params, Xs, Ps)
+        assert si.outer_iters == inf.outer_iters
+        assert relF(x, Xs.cpu().numpy()) <= 1e-12
+        check_assignment(p, Ps.cpu().numpy().astype(np.int64), Xs.cpu().numpy(), g)
+
+
+def test_batched_host_buffers_and_no_x(torch_cuda, ctx):
+    pairs = mixed_batch(2)
+    Xd, Pd, _ = run_batched(torch_cuda, ctx, pairs, None, device=True)
+    Xh, Ph, _ = run_batched(torch_cuda, ctx, pairs, None, device=False)
+    _, Pn, _ = run_batched(torch_cuda, ctx, pairs, None, device=True, want_x=False)
+    for a, b, c, d, e in zip(Xd, Xh, Pd, Ph, Pn):
+        assert np.array_equal(a, b) and np.array_equal(c, d) and np.array_equal(c, e)
+
+
+def test_batched_mixed_equal_accuracy(torch_cuda, ctx):
+    pairs = mixed_batch(3)
+    params = fr.fram_default_params(theta=10.0, precision=fr.FRAM_PREC_MIXED_BF16)
+    X, P, infos = run_batched(torch_cuda, ctx, pairs, params)
+    acc_m, acc_o = [], []
+    for g, x, p, inf in zip(pairs, X, P, infos):
+        ref = o.fram(g.A, g.B, theta=10.0)
+        acc_m.append(o.accuracy(p, g.truth))
+        acc_o.append(o.accuracy(ref.perm, g.truth))
+        assert abs(inf.objective - ref.objective) <= 1e-3 * abs(ref.objective), g.meta
+        assert abs(inf.objective - o.objective(g.A, g.B, p)) <= 1e-9 * abs(inf.objective)
+    assert np.mean(acc_m) >= np.mean(acc_o) - 0.005
+
+
+def test_batched_routes_large_pairs_and_rejects_invalid(torch_cuda, ctx):
+    torch = torch_cuda
+    pairs = [fi.small_er_pair(0), fi.er_pair(100, 0.1, noise=0.02, seed=4)]
+    X, P, infos = run_batched(torch, ctx, pairs, None)
+    for g, x, p, inf in zip(pairs, X, P, infos):
+        ref = o.fram(g.A, g.B, theta=10.0)
+        assert relF(x, ref.N) <= 1e-9
+        check_assignment(p, ref.perm, ref.N, g, inf, ref)
+    bad = fi.small_er_pair(1)
+    bad.A[0, 1] += 0.5                               # asymmetric
+    st, _ = fr.fram_solve_batched(ctx, [50, 50], [pairs[0].A, bad.A], [pairs[0].B, bad.B], None,
+                                  None, [np.empty(50, np.int32), np.empty(50, np.int32)],
+                                  check=False)
+    assert st == fr.FRAM_ERR_INVALID and "pair 1" in fr.fram_last_error(ctx)
+
+
+def test_batched_full_keypoint_workload_sampled(torch_cuda, ctx):
+    # 4096 keypoint pairs, n ~ U{10..64} with 0-20% outliers, theta = 2, FP32
+    # mixed batched; a 1% sample is re-solved by the oracle.
+    torch = torch_cuda
+    pairs = fi.keypoint_batch(4096, seed=7)
+    params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_BF16)
+    ns = [g.n for g in pairs]
+    As = [torch.from_numpy(g.A).cuda() for g in pairs]
+    Bs = [torch.from_numpy(g.B).cuda() for g in pairs]
+    Ps = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    _, infos = fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(pairs), size=41, replace=False)
+    acc_m, acc_o = [], []
+    for k in sample:
+        g = pairs[k]
+        p = Ps[k].cpu().numpy().astype(np.int64)
+        assert sorted(p.tolist()) == list(range(g.n))
+        ref = o.fram(g.A, g.B, theta=2.0)
+        acc_m.append(o.accuracy(p, g.truth))
+        acc_o.append(o.accuracy(ref.perm, g.truth))
+        assert abs(infos[k].objective - ref.objective) <= 1e-3 * abs(ref.objective)
+    assert np.mean(acc_m) >= np.mean(acc_o) - 0.005
