@@ -126,6 +126,18 @@ const char *fram_last_error(const fram_ctx *ctx);
 /* Number of this library's kernels launched on `ctx` since creation. */
 uint64_t fram_kernel_launches(const fram_ctx *ctx);
 
+/* Time limit of every device-side wait on `ctx` (grid barriers, mbarrier
+ * waits), in milliseconds (default 4000).  On expiry the waiting kernel
+ * records the failure, stops, and the call returns FRAM_ERR_TIMEOUT; the
+ * context stays usable.  FRAM_ERR_INVALID for limit_ms < 1. */
+fram_status fram_set_wait_limit(fram_ctx *ctx, int limit_ms);
+
+/* Failure-path self-test: launches `blocks` CTAs that wait at the library's
+ * grid barrier for one more CTA than exists, so the wait can only end by its
+ * time limit.  Returns FRAM_ERR_TIMEOUT (the expected outcome) after about
+ * the context's wait limit; FRAM_ERR_INVALID for blocks < 1 or > 64. */
+fram_status fram_selftest_wait_timeout(fram_ctx *ctx, int blocks);
+
 /* ------------------------------------------------------------ full solve */
 
 /* Solve one matching problem with FRAM (Alg. 1 + Alg. 2 + eq. 2).
@@ -157,17 +169,25 @@ fram_status fram_solve_batched(fram_ctx *ctx, int count, const int *n, const dou
 
 /* ------------------------------------------------------------- serving */
 
-/* Enqueue one problem for the context's continuous-batching scheduler.  A
- * and B (host or device) are copied into library-owned device slots before
- * the call returns.  Returns FRAM_ERR_BUSY when the request does not fit the
- * HBM budget and the waiting queue is full. */
+/* Enqueue one problem for the context's continuous-batching scheduler (a
+ * thread the context starts on first use).  A and B (host or device) are
+ * copied into library-owned memory before the call returns, so the caller
+ * may free them.  The scheduler admits waiting requests into device slots
+ * while the HBM budget (hbm_budget_bytes of fram_create; 0 = 60% of the
+ * memory free at first use) has room, keeps A, B, N and X resident until the
+ * request retires, and advances all admitted requests together, one outer
+ * iteration per tick, with their SDSN sweeps in one grouped launch.  Each
+ * request computes exactly what fram_solve computes with the same params (no
+ * K).  Returns FRAM_ERR_BUSY when the waiting queue is full. */
 fram_status fram_submit(fram_ctx *ctx, int n, const double *A, const double *B,
                         const fram_params *params, uint64_t *ticket);
 
 /* Collect a submitted problem.  Waits up to wait_ms milliseconds (0 = do not
- * wait, < 0 = wait until done).  Returns FRAM_NOT_READY while in flight;
- * FRAM_OK copies N (if X_out != NULL), perm and info out and retires the
- * ticket.  Unknown tickets give FRAM_ERR_INVALID. */
+ * wait, < 0 = wait until done).  Returns FRAM_NOT_READY while in flight.  On
+ * completion the ticket retires: FRAM_OK copies N (if X_out != NULL), perm
+ * and info out (host or device buffers; info.ms_total is the request's
+ * latency from submit to completion); a failed request returns its error.
+ * Unknown or retired tickets give FRAM_ERR_INVALID. */
 fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *perm_out,
                       fram_info *info, int wait_ms);
 
@@ -194,6 +214,16 @@ fram_status fram_gradient_lowp(fram_ctx *ctx, int n, const double *A, const doub
  * FRAM_ERR_DEGENERATE if max(X) <= 0. */
 fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double theta,
                       double gamma_tol, int max_sweeps, int *sweeps_out, double *gamma_out);
+
+/* SDSN (as fram_sdsn) of `count` independent problems in ONE grouped,
+ * cooperative launch: problem i (size n[i], device X[i] -> D[i]) runs on the
+ * same sub-grid fram_sdsn would give it, with its own barrier and stop test.
+ * This is the serving path's grouped SDSN.  Problems whose sub-grids do not
+ * all fit one co-resident wave return FRAM_ERR_INVALID.  sweeps_out and
+ * gamma_out (host arrays of count) may be NULL. */
+fram_status fram_sdsn_grouped(fram_ctx *ctx, int count, const int *n, const double *const *X,
+                              double *const *D, double theta, double gamma_tol, int max_sweeps,
+                              int *sweeps_out, double *gamma_out);
 
 /* Linear assignment of eq. 2 on W (n x n, device): perm maximises
  * sum_i W[i][perm[i]] (device int32 output).  value_out (host) may be NULL. */

@@ -82,6 +82,8 @@ def load(path: str | None = None):
         "fram_default_params": (None, [C.POINTER(FramParams)]),
         "fram_last_error": (C.c_char_p, [_P]),
         "fram_kernel_launches": (u64, [_P]),
+        "fram_set_wait_limit": (i, [_P, i]),
+        "fram_selftest_wait_timeout": (i, [_P, i]),
         "fram_solve": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P, C.POINTER(FramInfo)]),
         "fram_solve_batched": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P,
                                    C.POINTER(FramInfo)]),
@@ -90,6 +92,7 @@ def load(path: str | None = None):
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
         "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
+        "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
         "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d)]),
         "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
                                  sz]),
@@ -105,9 +108,10 @@ def load(path: str | None = None):
 def exported_symbols():
     """Names the header declares; used by the ABI test."""
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
-            "fram_kernel_launches", "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_assign",
-            "fram_sdsn_static"]
+            "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
+            "fram_solve", "fram_solve_batched", "fram_submit",
+            "fram_poll", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
+            "fram_assign", "fram_sdsn_static"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -170,6 +174,18 @@ def fram_last_error(ctx) -> str:
 
 def fram_kernel_launches(ctx) -> int:
     return int(load().fram_kernel_launches(ctx))
+
+
+def fram_set_wait_limit(ctx, limit_ms: int, check=True):
+    st = load().fram_set_wait_limit(ctx, limit_ms)
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def fram_selftest_wait_timeout(ctx, blocks: int = 4):
+    """Expected to return FRAM_ERR_TIMEOUT (no exception)."""
+    return load().fram_selftest_wait_timeout(ctx, blocks)
 
 
 def fram_solve(ctx, n, A, B, K=None, params=None, X_out=None, perm_out=None, check=True):
@@ -255,6 +271,20 @@ def fram_sdsn_static(n, X, D, theta, gamma_tol=1e-14, max_sweeps=200, stream=Non
     if check and st != FRAM_OK:
         raise FramError(st, msg)
     return st, sw.value, g.value, msg
+
+
+def fram_sdsn_grouped(ctx, ns, Xs, Ds, theta, gamma_tol=1e-14, max_sweeps=200, check=True):
+    count = len(ns)
+    n_arr = (C.c_int * count)(*ns)
+    x_arr = (_P * count)(*[_addr(x) for x in Xs])
+    d_arr = (_P * count)(*[_addr(x) for x in Ds])
+    sw = (C.c_int * count)()
+    g = (C.c_double * count)()
+    st = load().fram_sdsn_grouped(ctx, count, n_arr, x_arr, d_arr, theta, gamma_tol, max_sweeps,
+                                  C.cast(sw, _P), C.cast(g, _P))
+    if check:
+        _check(ctx, st)
+    return st, list(sw), list(g)
 
 
 def fram_assign(ctx, n, W, perm, check=True):

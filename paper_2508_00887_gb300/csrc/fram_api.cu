@@ -447,7 +447,36 @@ fram_status fram_destroy(fram_ctx* c) {
 
 const char* fram_last_error(const fram_ctx* c) { return c ? c->last_error.c_str() : ""; }
 
-uint64_t fram_kernel_launches(const fram_ctx* c) { return c ? c->launches : 0; }
+uint64_t fram_kernel_launches(const fram_ctx* c) { return c ? c->launches.load() : 0; }
+
+fram_status fram_set_wait_limit(fram_ctx* c, int limit_ms) {
+  if (!c || limit_ms < 1) return FRAM_ERR_INVALID;
+  c->wait_limit_ns = (uint64_t)limit_ms * 1000000ull;
+  return FRAM_OK;
+}
+
+fram_status fram_selftest_wait_timeout(fram_ctx* c, int blocks) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (blocks < 1 || blocks > 64) {
+    set_err(c, "fram_selftest_wait_timeout: 1 <= blocks <= 64");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, 1));
+  Workspace& w = c->ws;
+  // Small grids are co-resident on any GPU, so every CTA reaches the barrier.
+  FR_CUDA(cudaMemsetAsync(&w.scal->bar, 0, sizeof(GridBarrier), c->stream), "memset");
+  FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn.status, 0, sizeof(int), c->stream), "memset");
+  FR_LAUNCH(launch_wait_selftest(&w.scal->bar, &w.scal->iter.sdsn.status, blocks,
+                                 c->wait_limit_ns, c->stream),
+            "wait self-test kernel");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.sdsn.status, &w.scal->iter.sdsn.status, sizeof(int),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  return dev_status(c, w.hscal->iter.sdsn.status, "self-test wait");
+}
 
 fram_status fram_solve(fram_ctx* c, int n, const double* A, const double* B, const double* K,
                        const fram_params* params, double* X_out, int32_t* perm_out,
@@ -572,6 +601,86 @@ fram_status fram_sdsn(fram_ctx* c, int n, const double* X, double* D, double the
   FR_TRY(dev_status(c, st.status, "SDSN"));
   if (sweeps_out) *sweeps_out = st.sweeps;
   if (gamma_out) *gamma_out = st.gamma;
+  return FRAM_OK;
+}
+
+fram_status fram_sdsn_grouped(fram_ctx* c, int count, const int* n, const double* const* X,
+                              double* const* D, double theta, double gamma_tol, int max_sweeps,
+                              int* sweeps_out, double* gamma_out) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (count < 1 || count > 64 || !n || !X || !D || !(theta > 0.0) || max_sweeps < 1) {
+    set_err(c, "fram_sdsn_grouped: 1 <= count <= 64, theta > 0, max_sweeps >= 1 are required");
+    return FRAM_ERR_INVALID;
+  }
+  int nmax = 0, blocks = 0;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || !X[i] || !D[i] || !is_device_ptr(X[i]) || !is_device_ptr(D[i])) {
+      set_err(c, "fram_sdsn_grouped: problem %d needs n >= 1 and device X, D", i);
+      return FRAM_ERR_INVALID;
+    }
+    nmax = std::max(nmax, n[i]);
+    blocks += sdsn_grid_blocks(n[i], c->num_sms);
+  }
+  if (blocks > c->num_sms) {
+    set_err(c, "fram_sdsn_grouped: the sub-grids need %d CTAs, more than one wave", blocks);
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  // Per-problem scratch: partials, stats, barriers, max keys.
+  size_t per = sdsn_partials_elems(nmax, c->num_sms) * sizeof(double);
+  per = (per + 255) & ~(size_t)255;
+  const size_t hdr = 256;
+  char* buf = nullptr;
+  FR_CUDA(cudaMalloc(&buf, count * (per + hdr) + sdsn_group_desc_bytes(count)), "scratch");
+  struct Hdr {
+    SdsnStats st;
+    GridBarrier bar;
+    unsigned long long key;
+  };
+  std::vector<SdsnLaunch> L(count);
+  fram_status rs = FRAM_OK;
+  FR_CUDA(cudaMemsetAsync(buf, 0, count * hdr, c->stream), "memset");
+  for (int i = 0; i < count && rs == FRAM_OK; ++i) {
+    Hdr* h = reinterpret_cast<Hdr*>(buf + i * hdr);
+    if (launch_max(X[i], n[i], n[i], &h->key, c->stream) < 0) rs = FRAM_ERR_CUDA;
+    c->launches += 1;
+    L[i].n = n[i];
+    L[i].X = X[i];
+    L[i].ldx = n[i];
+    L[i].Y = D[i];
+    L[i].ldy = n[i];
+    L[i].theta = theta;
+    L[i].gamma_tol = gamma_tol;
+    L[i].max_sweeps = max_sweeps;
+    L[i].xmax_key = &h->key;
+    L[i].stats = &h->st;
+    L[i].partials = reinterpret_cast<double*>(buf + count * hdr + i * per);
+    L[i].barrier = &h->bar;
+    L[i].limit_ns = c->wait_limit_ns;
+  }
+  if (rs == FRAM_OK &&
+      launch_sdsn_group(L.data(), count, c->num_sms, buf + count * (hdr + per),
+                        sdsn_group_desc_bytes(count), c->num_sms, c->stream) < 0)
+    rs = FRAM_ERR_CUDA;
+  std::vector<Hdr> hh(count);
+  if (rs == FRAM_OK) {
+    c->launches += 1;
+    if (cudaMemcpy2DAsync(hh.data(), sizeof(Hdr), buf, hdr, sizeof(Hdr), count,
+                          cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rs = FRAM_ERR_CUDA;
+  }
+  if (rs == FRAM_ERR_CUDA) set_err(c, "fram_sdsn_grouped: %s", cudaGetErrorString(cudaGetLastError()));
+  cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  if (rs != FRAM_OK) return rs;
+  for (int i = 0; i < count; ++i) {
+    fram_status s1 = dev_status(c, hh[i].st.status, "grouped SDSN");
+    if (s1 != FRAM_OK) return s1;
+    if (sweeps_out) sweeps_out[i] = hh[i].st.sweeps;
+    if (gamma_out) gamma_out[i] = hh[i].st.gamma;
+  }
   return FRAM_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -49,15 +50,16 @@ struct Workspace {
 struct fram_ctx {
   int device = 0, num_sms = 0, cc_major = 0, cc_minor = 0;
   size_t budget = 0;
-  size_t serve_bytes = 0;  // device bytes held by serving slots
+  std::atomic<size_t> serve_bytes{0};  // device bytes held by serving slots
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evp[5] = {};  // phase boundaries inside one outer iteration
   std::string last_error;
-  uint64_t launches = 0;
+  std::atomic<uint64_t> launches{0};
   uint64_t wait_limit_ns = fram::kWaitLimitNs;
-  std::mutex mu;
+  std::mutex mu;        // serialises the synchronous entry points
+  std::mutex serve_mu;  // guards creation of the serving scheduler
   fram::Workspace ws;
   void* batched = nullptr;
   void* serve = nullptr;

@@ -288,6 +288,14 @@ __global__ void max_kernel(const double* __restrict__ X, int ldx, int n, unsigne
   if (threadIdx.x == 0 && bm > -INFINITY) atomicMax(out, ordered_key(bm));
 }
 
+// Waits at a grid barrier sized for gridDim.x + 1 CTAs: nothing can complete
+// it, so every CTA leaves through the time limit and records DEV_TIMEOUT.
+__global__ void wait_selftest_kernel(GridBarrier* bar, int* status, uint64_t limit_ns) {
+  __shared__ int s_flag;
+  unsigned gen = 0;
+  grid_sync(bar, gridDim.x + 1, gen, limit_ns, status, &s_flag);
+}
+
 int grid_rows(int rows) { return rows < 1 ? 1 : (rows < 1184 ? rows : 1184); }
 
 }  // namespace
@@ -329,6 +337,12 @@ int launch_update(double* N, int ldn, const double* D, int ldd, int n, double al
                   double* partials, unsigned* ticket, cudaStream_t s) {
   update_kernel<<<grid_rows(n), kRowThreads, 0, s>>>(N, ldn, D, ldd, n, alpha, partials, ticket,
                                                      st);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_wait_selftest(GridBarrier* bar, int* status, int blocks, uint64_t limit_ns,
+                         cudaStream_t s) {
+  wait_selftest_kernel<<<blocks, 32, 0, s>>>(bar, status, limit_ns);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -191,6 +191,13 @@ struct SdsnLaunch {
 size_t sdsn_partials_elems(int n, int max_blocks);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s);
+// Several problems (same precision pair) in one cooperative launch of at most
+// max_blocks CTAs; ddesc is device scratch of sdsn_group_desc_bytes(count).
+int launch_sdsn_group(const SdsnLaunch* L, int count, int max_blocks, void* ddesc,
+                      size_t ddesc_bytes, int num_sms, cudaStream_t s);
+size_t sdsn_group_desc_bytes(int count);
+// CTAs of the single-problem SDSN grid for size n (what fram_sdsn uses).
+int sdsn_grid_blocks(int n, int num_sms);
 
 int launch_update(double* N, int ldn, const double* D, int ldd, int n, double alpha,
                   IterStats* st, double* partials, unsigned* ticket, cudaStream_t s);
@@ -199,6 +206,9 @@ size_t update_partials_elems(int n);
 int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
                cudaStream_t s);
 size_t lap_workspace_bytes(int n);
+
+int launch_wait_selftest(GridBarrier* bar, int* status, int blocks, uint64_t limit_ns,
+                         cudaStream_t s);
 
 int launch_objective(const double* A, const double* B, const double* K, double lam, int n,
                      const int32_t* perm, ObjStats* st, double* partials, unsigned* ticket,

@@ -193,9 +193,9 @@ int launch_transpose_lp(const double* src, void* dst, int ld, int kind, cudaStre
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-static int launch_update_mixed(double* N, const double* D, int ld, int n, double alpha, void* Nt,
-                               int kind, double* partials, unsigned* ticket, IterStats* st,
-                               cudaStream_t s) {
+int launch_update_mixed(double* N, const double* D, int ld, int n, double alpha, void* Nt,
+                        int kind, double* partials, unsigned* ticket, IterStats* st,
+                        cudaStream_t s) {
   const int tiles = ((n + kT - 1) / kT) * ((n + kT - 1) / kT);
   const int grid = tiles < 1184 ? tiles : 1184;
   if (kind == 0)

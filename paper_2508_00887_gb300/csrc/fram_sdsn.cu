@@ -20,6 +20,8 @@
 // memory is touched only to load X and to store the result.
 #include <math.h>
 
+#include <vector>
+
 #include "fram_internal.cuh"
 
 namespace fram {
@@ -36,6 +38,7 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 template <typename T, typename TIn>
 struct SdsnK {
   int n, P, Q, tr, tc, resident;
+  int block0;  // grouped launches: first CTA of this problem
   int mode;  // 0: Y0 = (theta/2) X / max(X) (Alg. 2 step 1); 1: Y0 = X (continue a run)
   const TIn* X;
   int ldx;
@@ -117,7 +120,8 @@ __device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
 template <typename T, typename TIn, int MAXC, bool FIRST>
 __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int ldt, T* colacc,
                                           T* rowsum, const T* arow, const T* bcol, int nr,
-                                          int nc, int r0, int c0, int bi, int bj, T scale, int wb) {
+                                          int nc, int r0, int c0, int bi, int bj, T scale, int wb,
+                                          int blk, int nblk) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wacc = colacc + warp * p.tc;
   if (MAXC == 0)
@@ -183,20 +187,21 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
     double t = 0.0;
     for (int i = lane; i < nr; i += 32) t += (double)rowsum[i];
     t = warp_sum(t);
-    if (lane == 0) p.tpart[(size_t)wb * gridDim.x + blockIdx.x] = t;
+    if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = t;
   }
 }
 
+// The whole SDSN of one problem on CTAs blk = 0 .. nblk-1 of its (sub)grid.
 template <typename T, typename TIn, int MAXC>
-__global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int nblk,
+                                          unsigned char* smem) {
   __shared__ int s_flag;
   __shared__ double s_S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int bi = blockIdx.x / p.Q, bj = blockIdx.x % p.Q;
+  const int bi = blk / p.Q, bj = blk % p.Q;
   const int r0 = bi * p.tr, c0 = bj * p.tc;
   const int nr = max(0, min(p.tr, p.n - r0)), nc = max(0, min(p.tc, p.n - c0));
-  const unsigned nblocks = gridDim.x;
+  const unsigned nblocks = (unsigned)nblk;
 
   size_t off = 0;
   T* tile;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) 
   const double m = p.mode == 0 ? from_ordered_key(*p.xmax_key) : 1.0;
   const int max_sweeps = (p.gate != nullptr && p.gate->gamma <= p.gate_tol) ? 0 : p.max_sweeps;
   if (!(m > 0.0)) {
-    if (blockIdx.x == 0 && tid == 0) {
+    if (blk == 0 && tid == 0) {
       p.stats->status = DEV_DEGENERATE;
       p.stats->sweeps = 0;
       p.stats->converged = 0;
@@ -239,7 +244,7 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) 
   const T scale = (T)((p.theta / 2.0) / m);
 
   sdsn_pass<T, TIn, MAXC, true>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj,
-                                scale, 0);
+                                scale, 0, blk, nblk);
   unsigned epoch = 1;
   if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
 
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) 
     for (int i = tid; i < nr; i += kSdsnThreads) arow[i] = c1 - rowsum[i] * inv_n_t;
     __syncthreads();
     sdsn_pass<T, TIn, MAXC, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi,
-                                   bj, scale, rb ^ 1);
+                                   bj, scale, rb ^ 1, blk, nblk);
     ++k;
     ++epoch;
     if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
@@ -295,12 +300,36 @@ __global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) 
       for (int j = lane; j < nc; j += 32) dst[j] = src[j];
     }
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blk == 0 && tid == 0) {
     p.stats->sweeps = k;
     p.stats->gamma = g;
     p.stats->converged = (g <= p.gamma_tol) ? 1 : 0;
     p.stats->xmax = m;
   }
+}
+
+template <typename T, typename TIn, int MAXC>
+__global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_kernel(SdsnK<T, TIn> p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  sdsn_body<T, TIn, MAXC>(p, blockIdx.x, gridDim.x, smem);
+}
+
+// Several independent SDSN problems in one cooperative launch: problem j owns
+// CTAs [block0_j, block0_j + P_j Q_j) and its own partials and barrier, so
+// each problem advances at its own pace and stops on its own gamma.
+template <typename T, typename TIn, int MAXC>
+__global__ void __launch_bounds__(kSdsnThreads, 1) sdsn_group_kernel(const SdsnK<T, TIn>* probs,
+                                                                     int nprobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int lo = 0, hi = nprobs - 1;  // last problem with block0 <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].block0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const SdsnK<T, TIn> p = probs[lo];
+  const int nblk = p.P * p.Q;
+  if ((int)blockIdx.x - p.block0 >= nblk) return;  // spare CTA (not part of any sub-grid)
+  sdsn_body<T, TIn, MAXC>(p, (int)blockIdx.x - p.block0, nblk, smem);
 }
 
 // Grid shape: square P x Q with P*Q co-resident CTAs; a single CTA for small
@@ -377,7 +406,128 @@ int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   return launch_k<T, TIn, 0>(k, P * Q, smem, num_sms, s);
 }
 
+static_assert(sizeof(SdsnK<double, double>) <= 256, "group descriptor slot");
+
+template <typename T, typename TIn, int MAXC>
+int launch_group_k(const SdsnK<T, TIn>* dprobs, int nprobs, int nblocks, size_t smem,
+                   int num_sms, cudaStream_t s) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    if (cudaFuncSetAttribute(sdsn_group_kernel<T, TIn, MAXC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) !=
+        cudaSuccess)
+      return -1;
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sdsn_group_kernel<T, TIn, MAXC>,
+                                                      kSdsnThreads, kSmemCap) != cudaSuccess)
+      return -1;
+    per_sm = v;
+  }
+  if (per_sm < 1 || nblocks > per_sm * num_sms) return -1;
+  void* args[] = {(void*)&dprobs, &nprobs};
+  if (cudaLaunchCooperativeKernel((const void*)sdsn_group_kernel<T, TIn, MAXC>, dim3(nblocks),
+                                  dim3(kSdsnThreads), args, smem, s) != cudaSuccess)
+    return -1;
+  return 1;
+}
+
+template <typename T, typename TIn>
+int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* ddesc,
+                        size_t ddesc_bytes, int num_sms, cudaStream_t s) {
+  if (count < 1 || count > max_blocks) return -1;
+  // Sub-grid sides: each problem's preferred square grid, shrunk (largest
+  // first) until all sub-grids fit in one co-resident wave.
+  std::vector<int> g(count);
+  int total = 0;
+  for (int i = 0; i < count; ++i) {
+    int P, Q;
+    choose_grid(L[i].n, max_blocks, P, Q);
+    g[i] = P;
+    total += P * P;
+  }
+  while (total > max_blocks) {
+    int w = 0;
+    for (int i = 1; i < count; ++i)
+      if (g[i] > g[w]) w = i;
+    if (g[w] <= 1) return -1;
+    total -= g[w] * g[w];
+    --g[w];
+    total += g[w] * g[w];
+  }
+  std::vector<SdsnK<T, TIn>> ks(count);
+  size_t smem = 0;
+  int slots = 0, block0 = 0;
+  for (int i = 0; i < count; ++i) {
+    SdsnK<T, TIn>& k = ks[i];
+    const int P = g[i], Q = g[i];
+    const int tr = (L[i].n + P - 1) / P, tc = (L[i].n + Q - 1) / Q;
+    const bool resident = sdsn_smem_bytes<T>(tr, tc, true) <= kSmemCap;
+    const size_t sm = sdsn_smem_bytes<T>(tr, tc, resident);
+    if (sm > kSmemCap) return -1;
+    smem = sm > smem ? sm : smem;
+    const int sl = (tc + 31) / 32;
+    slots = sl > slots ? sl : slots;
+    k.n = L[i].n;
+    k.P = P;
+    k.Q = Q;
+    k.tr = tr;
+    k.tc = tc;
+    k.resident = resident ? 1 : 0;
+    k.block0 = block0;
+    block0 += P * Q;
+    k.mode = L[i].mode;
+    k.X = static_cast<const TIn*>(L[i].X);
+    k.ldx = L[i].ldx;
+    k.Y = static_cast<T*>(L[i].Y);
+    k.ldy = L[i].ldy;
+    k.theta = L[i].theta;
+    k.gamma_tol = L[i].gamma_tol;
+    k.max_sweeps = L[i].max_sweeps;
+    k.xmax_key = L[i].xmax_key;
+    k.gate = L[i].gate;
+    k.gate_tol = L[i].gate_tol;
+    k.stats = L[i].stats;
+    k.rpart = reinterpret_cast<T*>(L[i].partials);
+    k.cpart = k.rpart + (size_t)2 * Q * L[i].n;
+    k.tpart = L[i].partials + (size_t)2 * (P + Q) * L[i].n;
+    k.bar = L[i].barrier;
+    k.limit_ns = L[i].limit_ns;
+    if (cudaMemsetAsync(L[i].barrier, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
+  }
+  if (count * sizeof(SdsnK<T, TIn>) > ddesc_bytes) return -1;
+  if (cudaMemcpyAsync(ddesc, ks.data(), count * sizeof(SdsnK<T, TIn>), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return -1;
+  const SdsnK<T, TIn>* dk = static_cast<const SdsnK<T, TIn>*>(ddesc);
+  if (slots <= 4) return launch_group_k<T, TIn, 4>(dk, count, block0, smem, num_sms, s);
+  if (slots <= 24) return launch_group_k<T, TIn, 24>(dk, count, block0, smem, num_sms, s);
+  return launch_group_k<T, TIn, 0>(dk, count, block0, smem, num_sms, s);
+}
+
 }  // namespace
+
+int launch_sdsn_group(const SdsnLaunch* L, int count, int max_blocks, void* ddesc,
+                      size_t ddesc_bytes, int num_sms, cudaStream_t s) {
+  if (count < 1) return 0;
+  const bool in32 = L[0].in_fp32, out32 = L[0].out_fp32;
+  for (int i = 1; i < count; ++i)
+    if (L[i].in_fp32 != in32 || L[i].out_fp32 != out32) return -1;
+  if (!in32 && !out32)
+    return launch_sdsn_group_t<double, double>(L, count, max_blocks, ddesc, ddesc_bytes, num_sms, s);
+  if (in32 && out32)
+    return launch_sdsn_group_t<float, float>(L, count, max_blocks, ddesc, ddesc_bytes, num_sms, s);
+  if (in32 && !out32)
+    return launch_sdsn_group_t<double, float>(L, count, max_blocks, ddesc, ddesc_bytes, num_sms, s);
+  return -1;
+}
+
+size_t sdsn_group_desc_bytes(int count) { return (size_t)count * 256; }
+
+int sdsn_grid_blocks(int n, int num_sms) {
+  int P, Q;
+  choose_grid(n, num_sms, P, Q);
+  return P * Q;
+}
 
 size_t sdsn_partials_elems(int n, int max_blocks) {
   int g = 1;

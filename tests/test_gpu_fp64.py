@@ -272,3 +272,38 @@ def test_solve_medium_full_size_matches_oracle(torch_cuda, ctx):
     X, P, info = solve_gpu(torch_cuda, ctx, g)
     check_against_oracle(g, X, P, info, ref)
     assert info.total_sweeps == ref.total_sweeps
+
+
+def test_device_wait_timeout_returns_error_and_context_survives(torch_cuda, ctx):
+    # A grid barrier that can never complete (a flag nothing sets): the kernel
+    # must leave through its time limit with FRAM_ERR_TIMEOUT, without a fault,
+    # and the context must keep working afterwards.
+    import time
+    fr.fram_set_wait_limit(ctx, 200)
+    try:
+        t0 = time.perf_counter()
+        st = fr.fram_selftest_wait_timeout(ctx, 4)
+        dt = time.perf_counter() - t0
+        assert st == fr.FRAM_ERR_TIMEOUT
+        assert "wait" in fr.fram_last_error(ctx)
+        assert 0.15 < dt < 5.0
+    finally:
+        fr.fram_set_wait_limit(ctx, 4000)
+    g = fi.small_er_pair(0)
+    X, P, info = solve_gpu(torch_cuda, ctx, g)
+    assert o.accuracy(P, g.truth) == 1.0
+
+
+@pytest.mark.parametrize("ns", [[30], [300], [30, 80], [30, 150, 300], [97, 97, 97, 50]])
+def test_sdsn_grouped_equals_single(torch_cuda, ctx, ns):
+    # The serving path's grouped SDSN: every problem on its solo sub-grid must
+    # give exactly what fram_sdsn gives.
+    torch = torch_cuda
+    Xs = [dev(torch, np.random.default_rng(10 * k + n).random((n, n)) ** 2) for k, n in enumerate(ns)]
+    Ds = [torch.empty_like(x) for x in Xs]
+    _, sw, gm = fr.fram_sdsn_grouped(ctx, ns, Xs, Ds, 10.0, 1e-14, 200)
+    for k, n in enumerate(ns):
+        D1 = torch.empty_like(Xs[k])
+        _, s1, g1 = fr.fram_sdsn(ctx, n, Xs[k], D1, 10.0, 1e-14, 200)
+        assert sw[k] == s1 and gm[k] == g1
+        assert torch.equal(Ds[k], D1)
