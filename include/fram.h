@@ -73,10 +73,13 @@ typedef struct {
   double delta_tol;   /* outer stop: delta <= delta_tol (default 1e-6)              */
   double gamma_tol;   /* SDSN stop: gamma <= gamma_tol (default 1e-14)              */
   double polish_tol;  /* mixed paths: FP64 polish runs while gamma > polish_tol     */
-  double stall_ratio; /* mixed paths: also stop at the rounding floor, i.e. when     */
-  double stall_below; /* delta <= stall_below and delta > stall_ratio * previous     */
-                      /* delta (defaults 0.9 and 1e-3; stall_ratio = 0 disables).   */
-                      /* The FP64 path ignores both.                                 */
+  double mixed_delta_tol; /* mixed paths stop at delta <= max(delta_tol, this)       */
+                          /* (default 5e-4): BF16/TF32 rounding of N and T puts a    */
+                          /* floor under delta (~1e-4 BF16, ~1e-5 TF32 at n = 1000)   */
+  double stall_ratio; /* mixed paths, safeguard: also stop once delta <= stall_below */
+  double stall_below; /* and delta > stall_ratio * previous delta (defaults 0.9 and  */
+                      /* 1e-2; stall_ratio = 0 disables).  The FP64 path ignores     */
+                      /* all three.                                                  */
   int max_outer;      /* outer-iteration cap (default 100)                          */
   int max_sweeps;     /* SDSN sweep cap per call (default 200)                      */
   int max_polish;     /* mixed paths: FP64 polish sweep cap per call (default 0)    */

@@ -39,7 +39,8 @@ STATUS_NAMES = {0: "FRAM_OK", 1: "FRAM_NOT_READY", -1: "FRAM_ERR_INVALID", -2: "
 class FramParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("alpha", C.c_double), ("theta", C.c_double),
                 ("delta_tol", C.c_double), ("gamma_tol", C.c_double), ("polish_tol", C.c_double),
-                ("stall_ratio", C.c_double), ("stall_below", C.c_double), ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
+                ("mixed_delta_tol", C.c_double), ("stall_ratio", C.c_double),
+                ("stall_below", C.c_double), ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("reserved", C.c_int)]
 
 

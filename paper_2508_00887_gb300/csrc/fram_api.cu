@@ -153,6 +153,7 @@ fram_status check_params(fram_ctx* c, const fram_params& p) {
   if (!(p.alpha > 0.0 && p.alpha <= 1.0) || !(p.theta > 0.0) || !isfinite(p.theta) ||
       !isfinite(p.lambda) || !(p.delta_tol >= 0.0) || !(p.gamma_tol == p.gamma_tol) ||
       !(p.stall_ratio >= 0.0 && p.stall_ratio <= 1.0) || !(p.stall_below >= 0.0) ||
+      !(p.mixed_delta_tol >= 0.0) ||
       p.max_outer < 1 || p.max_sweeps < 1 || p.max_polish < 0 || p.init < 0 || p.init > 2 ||
       p.precision < FRAM_PREC_FP64 || p.precision > FRAM_PREC_MIXED_BF16 || p.reserved != 0) {
     set_err(c, "invalid fram_params");
@@ -378,8 +379,9 @@ void fram_default_params(fram_params* p) {
   p->delta_tol = 1e-6;
   p->gamma_tol = 1e-14;
   p->polish_tol = 1e-6;
+  p->mixed_delta_tol = 5e-4;
   p->stall_ratio = 0.9;
-  p->stall_below = 1e-3;
+  p->stall_below = 1e-2;
   p->max_outer = 100;
   p->max_sweeps = 200;
   p->max_polish = 0;

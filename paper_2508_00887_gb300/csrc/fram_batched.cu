@@ -49,7 +49,7 @@ struct BatchArgs {
   int32_t* perm;
   BatchInfo* info;
   unsigned* queue;
-  double lam, alpha, theta, delta_tol, gamma_tol, stall_ratio, stall_below;
+  double lam, alpha, theta, delta_tol, gamma_tol, mixed_delta_tol, stall_ratio, stall_below;
   int max_outer, max_sweeps, use_stall;
 };
 
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       nn2 = bsum<NT>(nn2, red);
       delta = sqrt(d2) / sqrt(nn2);
       ++t;
-      if (delta <= a.delta_tol) break;
+      if (delta <= a.delta_tol || (a.use_stall && delta <= a.mixed_delta_tol)) break;
       if (a.use_stall && a.stall_ratio > 0.0 && delta <= a.stall_below &&
           delta > a.stall_ratio * prev_delta)
         break;
@@ -706,6 +706,7 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
   a.theta = p.theta;
   a.delta_tol = p.delta_tol;
   a.gamma_tol = fp32 ? std::max(p.polish_tol, p.gamma_tol) : p.gamma_tol;
+  a.mixed_delta_tol = p.mixed_delta_tol;
   a.stall_ratio = p.stall_ratio;
   a.stall_below = p.stall_below;
   a.max_outer = p.max_outer;

@@ -324,9 +324,10 @@ fram_status solve_mixed_loop(fram_ctx* c, int n, bool has_K, const fram_params& 
     inf->gamma = it.polish.gamma;
     inf->sdsn_converged_last = it.polish.gamma <= p.gamma_tol ? 1 : 0;
     inf->delta = it.delta;
-    if (it.delta <= p.delta_tol) break;
-    // Rounding floor of the low-precision gradient: delta stops contracting
-    // (it settles on a short cycle) well above delta_tol.
+    // Reading (ix): the BF16/TF32 gradient puts a floor under delta (delta
+    // settles on a short cycle), so the mixed paths stop at mixed_delta_tol,
+    // or earlier if delta stops contracting.
+    if (it.delta <= p.delta_tol || it.delta <= p.mixed_delta_tol) break;
     if (p.stall_ratio > 0.0 && it.delta <= p.stall_below && it.delta > p.stall_ratio * prev_delta)
       break;
     prev_delta = it.delta;

@@ -19,6 +19,8 @@
 // tile fits in shared memory it stays there for all sweeps, and global
 // memory is touched only to load X and to store the result.
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -39,6 +41,7 @@ template <typename T, typename TIn>
 struct SdsnK {
   int n, P, Q, tr, tc, resident;
   int block0;  // grouped launches: first CTA of this problem
+  int vec_x, vec_y;  // X / Y rows can be accessed with 16-byte (8-byte) vectors
   int mode;  // 0: Y0 = (theta/2) X / max(X) (Alg. 2 step 1); 1: Y0 = X (continue a run)
   const TIn* X;
   int ldx;
@@ -112,46 +115,69 @@ __device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
   return *s_flag != 0;
 }
 
+// VEC consecutive elements of U at p: one 16/8/4-byte access when `vec`
+// (the address is then VEC*sizeof(U)-aligned), element by element otherwise
+// or when the vector would cross `lim` (elements valid: p[0 .. lim-1]).
+template <typename U, int V>
+__device__ __forceinline__ void vec_load(const U* p, bool vec, int lim, U (&out)[V]) {
+  if (vec && lim >= V) {
+    if constexpr (V * sizeof(U) == 16) {
+      const uint4 r = *reinterpret_cast<const uint4*>(p);
+      memcpy(out, &r, 16);
+      return;
+    } else if constexpr (V * sizeof(U) == 8) {
+      const uint2 r = *reinterpret_cast<const uint2*>(p);
+      memcpy(out, &r, 8);
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) out[v] = v < lim ? p[v] : U(0);
+}
+
+template <typename U, int V>
+__device__ __forceinline__ void vec_store(U* p, bool vec, int lim, const U (&in)[V]) {
+  if (vec && lim >= V) {
+    if constexpr (V * sizeof(U) == 16) {
+      uint4 r;
+      memcpy(&r, in, 16);
+      *reinterpret_cast<uint4*>(p) = r;
+      return;
+    } else if constexpr (V * sizeof(U) == 8) {
+      uint2 r;
+      memcpy(&r, in, 8);
+      *reinterpret_cast<uint2*>(p) = r;
+      return;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+    if (v < lim) p[v] = in[v];
+}
+
 // One pass over the tile.  FIRST: Y = (theta/2) X / m (mode 0) or Y = X
 // (mode 1).  Otherwise the fused P1+P2 sweep.  Both accumulate the new
-// tile's sums and publish them into partial buffer `wb`.  MAXC > 0: lane l
-// owns columns l + 32 s (s < MAXC) and keeps their sums in registers;
-// MAXC == 0: per-warp column sums accumulate in shared memory.
+// tile's sums and publish them into partial buffer `wb`.
+// MAXC > 0: lane l owns the 16-byte column groups l + 32 s (s < MAXC) of
+// VEC elements, moves them with vector accesses and keeps their column sums
+// in registers; for FP32 the next row's groups are loaded before the current
+// row is computed, so each warp keeps two rows of loads in flight.
+// MAXC == 0 (very wide tiles): one element per lane step, per-warp column
+// sums in shared memory.
 template <typename T, typename TIn, int MAXC, bool FIRST>
 __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int ldt, T* colacc,
                                           T* rowsum, const T* arow, const T* bcol, int nr,
                                           int nc, int r0, int c0, int bi, int bj, T scale, int wb,
-                                          int blk, int nblk) {
+                                          int blk, int nblk, T cS) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wacc = colacc + warp * p.tc;
-  if (MAXC == 0)
+  if constexpr (MAXC == 0) {
     for (int j = lane; j < nc; j += 32) wacc[j] = T(0);
-  T cacc[MAXC > 0 ? MAXC : 1];
-#pragma unroll
-  for (int s = 0; s < (MAXC > 0 ? MAXC : 1); ++s) cacc[s] = T(0);
-
-  for (int i = warp; i < nr; i += kSdsnWarps) {
-    T* row = tile + (size_t)i * ldt;
-    const TIn* xrow = FIRST ? p.X + (size_t)(r0 + i) * p.ldx + c0 : nullptr;
-    T ai = T(0);
-    if (!FIRST) ai = arow[i];
-    T racc = T(0);
-    if (MAXC > 0) {
-#pragma unroll
-      for (int s = 0; s < MAXC; ++s) {
-        const int j = lane + 32 * s;
-        if (j < nc) {
-          T y;
-          if (FIRST)
-            y = p.mode == 0 ? (T)xrow[j] * scale : (T)xrow[j];
-          else
-            y = relu((row[j] + ai) - bcol[j]);
-          row[j] = y;
-          racc += y;
-          cacc[s] += y;
-        }
-      }
-    } else {
+    for (int i = warp; i < nr; i += kSdsnWarps) {
+      T* row = tile + (size_t)i * ldt;
+      const TIn* xrow = FIRST ? p.X + (size_t)(r0 + i) * p.ldx + c0 : nullptr;
+      const T ai = FIRST ? T(0) : arow[i] + cS;
+      T racc = T(0);
       for (int j = lane; j < nc; j += 32) {
         T y;
         if (FIRST)
@@ -162,15 +188,82 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
         racc += y;
         wacc[j] += y;
       }
+      racc = warp_sum(racc);
+      if (lane == 0) rowsum[i] = racc;
     }
-    racc = warp_sum(racc);
-    if (lane == 0) rowsum[i] = racc;
-  }
-  if (MAXC > 0) {
+  } else {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr bool PREF = sizeof(T) == 4 && MAXC <= 6;
+    // Can the row source / tile be accessed with vectors?
+    const bool vsrc = FIRST ? p.vec_x != 0 : (p.resident != 0 || p.vec_y != 0);
+    const bool vdst = p.resident != 0 || p.vec_y != 0;
+    T cacc[MAXC][VEC];
+#pragma unroll
+    for (int s = 0; s < MAXC; ++s)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) cacc[s][v] = T(0);
+    T cur[MAXC][VEC], nxt[MAXC][VEC];
+    auto load_row = [&](int i, T (&dst)[MAXC][VEC]) {
+#pragma unroll
+      for (int s = 0; s < MAXC; ++s) {
+        const int j0 = (lane + 32 * s) * VEC;
+        if (j0 < nc) {
+          if (FIRST) {
+            TIn xv[VEC];
+            vec_load<TIn, VEC>(p.X + (size_t)(r0 + i) * p.ldx + c0 + j0, vsrc, nc - j0, xv);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) dst[s][v] = (T)xv[v];
+          } else {
+            vec_load<T, VEC>(tile + (size_t)i * ldt + j0, vsrc, nc - j0, dst[s]);
+          }
+        }
+      }
+    };
+    int i = warp;
+    if (i < nr) load_row(i, cur);
+    for (; i < nr; i += kSdsnWarps) {
+      const int inext = i + kSdsnWarps;
+      if (PREF && inext < nr) load_row(inext, nxt);
+      T* row = tile + (size_t)i * ldt;
+      const T ai = FIRST ? T(0) : arow[i] + cS;
+      T racc = T(0);
+#pragma unroll
+      for (int s = 0; s < MAXC; ++s) {
+        const int j0 = (lane + 32 * s) * VEC;
+        if (j0 < nc) {
+          T bv[VEC];
+          if (!FIRST) vec_load<T, VEC>(bcol + j0, true, nc - j0, bv);
+          T y[VEC];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            if (FIRST)
+              y[v] = p.mode == 0 ? cur[s][v] * scale : cur[s][v];
+            else
+              y[v] = relu((cur[s][v] + ai) - bv[v]);
+            if (j0 + v >= nc) y[v] = T(0);
+            racc += y[v];
+            cacc[s][v] += y[v];
+          }
+          vec_store<T, VEC>(row + j0, vdst, nc - j0, y);
+        }
+      }
+      racc = warp_sum(racc);
+      if (lane == 0) rowsum[i] = racc;
+      if (PREF) {
+#pragma unroll
+        for (int s = 0; s < MAXC; ++s)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) cur[s][v] = nxt[s][v];
+      } else if (inext < nr) {
+        load_row(inext, cur);
+      }
+    }
 #pragma unroll
     for (int s = 0; s < MAXC; ++s) {
-      const int j = lane + 32 * s;
-      if (j < nc) wacc[j] = cacc[s];  // zeros for warps that had no row
+      const int j0 = (lane + 32 * s) * VEC;
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+        if (j0 + v < nc) wacc[j0 + v] = cacc[s][v];  // zeros for warps that had no row
     }
   }
   __syncthreads();
@@ -244,7 +337,7 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
   const T scale = (T)((p.theta / 2.0) / m);
 
   sdsn_pass<T, TIn, MAXC, true>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj,
-                                scale, 0, blk, nblk);
+                                scale, 0, blk, nblk, T(0));
   unsigned epoch = 1;
   if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
 
@@ -271,8 +364,10 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
       T acc = T(0);
 #pragma unroll
       for (int q = 0; q < kMaxGrid; ++q) acc += v[q];
+      // a_i = 1/n + S/n^2 - r_i/n: the S term is added in the pass, once S
+      // is known, so that no extra barrier is needed here.
       if (is_row)
-        rowsum[idx] = acc;
+        arow[idx] = inv_n_t - acc * inv_n_t;
       else
         bcol[idx] = acc * inv_n_t;
     }
@@ -283,21 +378,23 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
       if (g <= p.gamma_tol) break;
     }
     if (k >= max_sweeps) break;
-    const T c1 = (T)(inv_n + S * inv_n2);
-    for (int i = tid; i < nr; i += kSdsnThreads) arow[i] = c1 - rowsum[i] * inv_n_t;
-    __syncthreads();
     sdsn_pass<T, TIn, MAXC, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi,
-                                   bj, scale, rb ^ 1, blk, nblk);
+                                   bj, scale, rb ^ 1, blk, nblk, (T)(S * inv_n2));
     ++k;
     ++epoch;
     if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
   }
 
   if (p.resident) {
+    constexpr int VEC = 16 / (int)sizeof(T);
     for (int i = warp; i < nr; i += kSdsnWarps) {
       T* dst = p.Y + (size_t)(r0 + i) * p.ldy + c0;
       const T* src = tile + (size_t)i * ldt;
-      for (int j = lane; j < nc; j += 32) dst[j] = src[j];
+      for (int j0 = lane * VEC; j0 < nc; j0 += 32 * VEC) {
+        T v[VEC];
+        vec_load<T, VEC>(src + j0, true, nc - j0, v);
+        vec_store<T, VEC>(dst + j0, p.vec_y != 0, nc - j0, v);
+      }
     }
   }
   if (blk == 0 && tid == 0) {
@@ -345,6 +442,30 @@ void choose_grid(int n, int max_blocks, int& P, int& Q) {
   P = Q = g < lim ? g : lim;
 }
 
+// Tile width: ceil(n / Q) rounded up to whole 16-byte groups, so every
+// tile starts on a group boundary.
+template <typename T>
+int tile_cols(int n, int Q) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  const int tc = (n + Q - 1) / Q;
+  return (tc + VEC - 1) / VEC * VEC;
+}
+
+// 16-byte groups per lane for a tile width: 0 selects the scalar path.
+template <typename T>
+int vec_slots(int tc) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  const int sl = (tc + 32 * VEC - 1) / (32 * VEC);
+  return sl <= 2 ? 2 : sl <= 6 ? 6 : sl <= 12 ? 12 : 0;
+}
+
+template <typename T, typename TIn>
+void set_vec_flags(SdsnK<T, TIn>& k) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  k.vec_x = (reinterpret_cast<uintptr_t>(k.X) % (VEC * sizeof(TIn)) == 0) && (k.ldx % VEC == 0);
+  k.vec_y = (reinterpret_cast<uintptr_t>(k.Y) % 16 == 0) && (k.ldy % VEC == 0);
+}
+
 template <typename T, typename TIn, int MAXC>
 int launch_k(SdsnK<T, TIn>& k, int nblocks, size_t smem, int num_sms, cudaStream_t s) {
   static int per_sm = -1;  // occupancy does not depend on the (capped) smem size here
@@ -372,7 +493,7 @@ int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   SdsnK<T, TIn> k{};
   int P, Q;
   choose_grid(L.n, num_sms, P, Q);
-  const int tr = (L.n + P - 1) / P, tc = (L.n + Q - 1) / Q;
+  const int tr = (L.n + P - 1) / P, tc = tile_cols<T>(L.n, Q);
   const bool resident = sdsn_smem_bytes<T>(tr, tc, true) <= kSmemCap;
   const size_t smem = sdsn_smem_bytes<T>(tr, tc, resident);
   if (smem > kSmemCap) return -1;  // tile rows too long even for streaming
@@ -400,10 +521,13 @@ int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   k.bar = L.barrier;
   k.limit_ns = L.limit_ns;
   if (cudaMemsetAsync(L.barrier, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
-  const int slots = (tc + 31) / 32;
-  if (slots <= 4) return launch_k<T, TIn, 4>(k, P * Q, smem, num_sms, s);
-  if (slots <= 24) return launch_k<T, TIn, 24>(k, P * Q, smem, num_sms, s);
-  return launch_k<T, TIn, 0>(k, P * Q, smem, num_sms, s);
+  set_vec_flags(k);
+  switch (vec_slots<T>(tc)) {
+    case 2: return launch_k<T, TIn, 2>(k, P * Q, smem, num_sms, s);
+    case 6: return launch_k<T, TIn, 6>(k, P * Q, smem, num_sms, s);
+    case 12: return launch_k<T, TIn, 12>(k, P * Q, smem, num_sms, s);
+    default: return launch_k<T, TIn, 0>(k, P * Q, smem, num_sms, s);
+  }
 }
 
 static_assert(sizeof(SdsnK<double, double>) <= 256, "group descriptor slot");
@@ -460,13 +584,13 @@ int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* dd
   for (int i = 0; i < count; ++i) {
     SdsnK<T, TIn>& k = ks[i];
     const int P = g[i], Q = g[i];
-    const int tr = (L[i].n + P - 1) / P, tc = (L[i].n + Q - 1) / Q;
+    const int tr = (L[i].n + P - 1) / P, tc = tile_cols<T>(L[i].n, Q);
     const bool resident = sdsn_smem_bytes<T>(tr, tc, true) <= kSmemCap;
     const size_t sm = sdsn_smem_bytes<T>(tr, tc, resident);
     if (sm > kSmemCap) return -1;
     smem = sm > smem ? sm : smem;
-    const int sl = (tc + 31) / 32;
-    slots = sl > slots ? sl : slots;
+    const int sl = vec_slots<T>(tc);
+    slots = (sl == 0 || slots == 0 && i > 0) ? 0 : (sl > slots ? sl : slots);
     k.n = L[i].n;
     k.P = P;
     k.Q = Q;
@@ -492,6 +616,7 @@ int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* dd
     k.tpart = L[i].partials + (size_t)2 * (P + Q) * L[i].n;
     k.bar = L[i].barrier;
     k.limit_ns = L[i].limit_ns;
+    set_vec_flags(k);
     if (cudaMemsetAsync(L[i].barrier, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
   }
   if (count * sizeof(SdsnK<T, TIn>) > ddesc_bytes) return -1;
@@ -499,9 +624,12 @@ int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* dd
                       s) != cudaSuccess)
     return -1;
   const SdsnK<T, TIn>* dk = static_cast<const SdsnK<T, TIn>*>(ddesc);
-  if (slots <= 4) return launch_group_k<T, TIn, 4>(dk, count, block0, smem, num_sms, s);
-  if (slots <= 24) return launch_group_k<T, TIn, 24>(dk, count, block0, smem, num_sms, s);
-  return launch_group_k<T, TIn, 0>(dk, count, block0, smem, num_sms, s);
+  switch (slots) {
+    case 2: return launch_group_k<T, TIn, 2>(dk, count, block0, smem, num_sms, s);
+    case 6: return launch_group_k<T, TIn, 6>(dk, count, block0, smem, num_sms, s);
+    case 12: return launch_group_k<T, TIn, 12>(dk, count, block0, smem, num_sms, s);
+    default: return launch_group_k<T, TIn, 0>(dk, count, block0, smem, num_sms, s);
+  }
 }
 
 }  // namespace

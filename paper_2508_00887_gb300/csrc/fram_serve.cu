@@ -393,7 +393,8 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       r->info.gamma = r->mixed ? it.polish.gamma : it.sdsn.gamma;
       r->info.sdsn_converged_last = r->info.gamma <= r->p.gamma_tol ? 1 : 0;
       r->info.delta = it.delta;
-      bool stop = it.delta <= r->p.delta_tol || r->t >= r->p.max_outer;
+      bool stop = it.delta <= r->p.delta_tol || r->t >= r->p.max_outer ||
+                  (r->mixed && it.delta <= r->p.mixed_delta_tol);
       if (r->mixed && r->p.stall_ratio > 0.0 && it.delta <= r->p.stall_below &&
           it.delta > r->p.stall_ratio * r->prev_delta)
         stop = true;

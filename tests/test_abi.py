@@ -68,8 +68,8 @@ int main(void) {{
 
 @pytest.mark.parametrize("cname,pystruct,cfields", [
     ("fram_params", fr.FramParams,
-     ["lambda", "alpha", "theta", "delta_tol", "gamma_tol", "polish_tol", "stall_ratio",
-      "stall_below", "max_outer",
+     ["lambda", "alpha", "theta", "delta_tol", "gamma_tol", "polish_tol", "mixed_delta_tol",
+      "stall_ratio", "stall_below", "max_outer",
       "max_sweeps", "max_polish", "precision", "init", "reserved"]),
     ("fram_info", fr.FramInfo,
      ["outer_iters", "total_sweeps", "polish_sweeps", "sdsn_converged_last", "lap_augmentations",

@@ -90,7 +90,7 @@ def check_equal_accuracy(g, ref, X, P, info):
     acc_o = o.accuracy(ref.perm, g.truth)
     acc_m = o.accuracy(P, g.truth)
     assert acc_m >= acc_o - 0.005
-    assert abs(info.objective - ref.objective) <= 1e-3 * abs(ref.objective)
+    assert info.objective >= ref.objective - 1e-3 * abs(ref.objective)  # not worse
     assert sorted(P.tolist()) == list(range(g.n))
     # the objective the kernels report is the one of the returned permutation
     assert abs(info.objective - o.objective(g.A, g.B, P)) <= 1e-9 * abs(info.objective)
@@ -149,8 +149,9 @@ def test_mixed_polish_reaches_fp64_tolerance(torch_cuda, ctx):
 
 def test_mixed_stops_at_rounding_floor(torch_cuda, ctx):
     # BF16 gradients put a floor under delta (about 1e-4 at n = 1000), far
-    # above delta_tol = 1e-6: the rounding-floor rule stops the loop once
-    # delta stops contracting; with the rule disabled the loop runs to the cap.
+    # above delta_tol = 1e-6: the mixed paths stop at mixed_delta_tol; with it
+    # disabled the stall safeguard stops the loop once delta stops contracting;
+    # with both disabled the loop runs to the cap.
     torch = torch_cuda
     g = fi.medium_er_pair(0)
     n = g.n
@@ -160,8 +161,11 @@ def test_mixed_stops_at_rounding_floor(torch_cuda, ctx):
     p = fr.fram_default_params(theta=g.theta, precision=fr.FRAM_PREC_MIXED_BF16, max_polish=4,
                                max_outer=60)
     _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
-    assert info.outer_iters < 30 and info.delta <= p.stall_below
+    assert info.outer_iters < 20 and info.delta <= p.mixed_delta_tol
     assert o.accuracy(P.cpu().numpy(), g.truth) == 1.0
+    p.mixed_delta_tol = 0.0
+    _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
+    assert info.outer_iters < 60 and info.delta <= p.stall_below
     p.stall_ratio = 0.0
     _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
     assert info.outer_iters == 60
