@@ -490,6 +490,8 @@ def run_ours(args):
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "solve": {"outer_iters": last.outer_iters, "total_sweeps": last.total_sweeps,
                       "polish_sweeps": last.polish_sweeps, "objective": last.objective,
+                      "lap_augmentations": last.lap_augmentations,
+                      "lap_auction_phases": last.lap_auction_phases,
                       "accuracy": o.accuracy(perm, g.truth)},
         }
         if fp64 is not None:

@@ -33,6 +33,8 @@ class GraphPair:
     truth: np.ndarray          # int64[n]; -1 where a node has no true partner
     theta: float               # the paper's setting: 2 dense, 10 sparse (Sec. 7)
     meta: dict = field(default_factory=dict)
+    F: np.ndarray | None = None    # n x d node attributes of the first graph
+    Ft: np.ndarray | None = None   # n x d node attributes of the second graph
 
     @property
     def n(self) -> int:
@@ -130,6 +132,29 @@ def gaussian_pair(n: int, jitter: float = 0.01, seed: int = 0, theta: float = 2.
     Q = Q + rng.normal(0.0, jitter, size=Q.shape)
     return GraphPair(_kernel_from_points(P), _kernel_from_points(Q), perm, theta,
                      dict(kind="gaussian", n=n, jitter=jitter, seed=seed))
+
+
+def _descriptors(rng: np.random.Generator, n: int, d: int) -> np.ndarray:
+    """Nonnegative unit-norm rows, like normalised gradient histograms."""
+    F = np.abs(rng.normal(0.0, 1.0, size=(n, d)))
+    return F / np.linalg.norm(F, axis=1, keepdims=True)
+
+
+def attributed_pair(n: int, d: int = 128, desc_noise: float = 0.5, jitter: float = 0.01,
+                    seed: int = 0, theta: float = 2.0) -> GraphPair:
+    """Dense Gaussian-kernel pair (as ``gaussian_pair``) whose nodes also carry
+    d-dimensional descriptors.  Node p[i] of the second graph gets node i's
+    descriptor plus N(0, desc_noise / sqrt(d)) per component, clamped at zero
+    and renormalised, so both sides stay nonnegative with unit norm."""
+    g = gaussian_pair(n, jitter=jitter, seed=seed, theta=theta)
+    rng = np.random.default_rng(seed + 1_000_003)
+    F = _descriptors(rng, n, d)
+    Ft = np.empty_like(F)
+    noisy = np.maximum(F + rng.normal(0.0, desc_noise / np.sqrt(d), size=F.shape), 0.0)
+    Ft[g.truth] = noisy / np.maximum(np.linalg.norm(noisy, axis=1, keepdims=True), 1e-300)
+    g.F, g.Ft = F, Ft
+    g.meta.update(kind="attributed", d=d, desc_noise=desc_noise)
+    return g
 
 
 def keypoint_pair(rng: np.random.Generator, n_min: int = 10, n_max: int = 64,

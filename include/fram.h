@@ -95,7 +95,8 @@ typedef struct {
   int polish_sweeps;        /* FP64 polish sweeps (mixed paths)                 */
   int sdsn_converged_last;  /* 1 if the last SDSN call reached gamma_tol        */
   int lap_augmentations;    /* rows placed by augmenting paths (0: argmax path) */
-  int reserved;
+  int lap_auction_phases;   /* epsilon-scaling auction phases run before them,
+                               -1 if the auction was not needed              */
   double delta;             /* last delta                                       */
   double gamma;             /* gamma of the last SDSN output                    */
   double objective;         /* Phi at the permutation, unscaled inputs (eq. 1)  */
@@ -201,6 +202,18 @@ fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *pe
 fram_status fram_gradient(fram_ctx *ctx, int n, const double *A, const double *N, const double *B,
                           const double *K, double lambda, double *X);
 
+/* Node-attribute affinity K = F Ft^T: the node term <N, F F~^T> of eq. 1,
+ * whose gradient lambda F F~^T enters eq. 3.  K[i][j] is the inner product
+ * of node i's attribute vector in G with node j's in G~.
+ *   F, Ft : n x d row-major FP64 device arrays (caller-owned, read only).
+ *   K     : n x n row-major FP64 device array (caller-owned), written.
+ * Pass K to fram_solve; nonnegative attributes (descriptor histograms, for
+ * instance) give the nonnegative K it requires.  Each entry is summed in
+ * FP64 over k = 0..d-1 in order.  Errors: FRAM_ERR_INVALID for n < 1, d < 1
+ * or null/host pointers. */
+fram_status fram_node_affinity(fram_ctx *ctx, int n, int d, const double *F, const double *Ft,
+                               double *K);
+
 /* Gradient of eq. 3 as the mixed paths form it: A, N, B (FP64, device) are
  * rounded to BF16 (precision = FRAM_PREC_MIXED_BF16) or TF32
  * (FRAM_PREC_MIXED_TF32); T = A N is accumulated in FP32 on the tensor cores
@@ -228,9 +241,15 @@ fram_status fram_sdsn_grouped(fram_ctx *ctx, int count, const int *n, const doub
                               double *const *D, double theta, double gamma_tol, int max_sweeps,
                               int *sweeps_out, double *gamma_out);
 
-/* Linear assignment of eq. 2 on W (n x n, device): perm maximises
- * sum_i W[i][perm[i]] (device int32 output).  value_out (host) may be NULL. */
-fram_status fram_assign(fram_ctx *ctx, int n, const double *W, int32_t *perm, double *value_out);
+/* Linear assignment of eq. 2 on W (n x n, device, finite): perm maximises
+ * sum_i W[i][perm[i]] (device int32 output; among optimal permutations the
+ * one returned is unspecified).  value_out (host) receives that sum and
+ * auction_phases_out (host) the number of epsilon-scaling auction phases
+ * run before the final augmenting paths (-1: none were needed); either may
+ * be NULL.  FRAM_ERR_TIMEOUT if the search did not terminate (non-finite
+ * W). */
+fram_status fram_assign(fram_ctx *ctx, int n, const double *W, int32_t *perm, double *value_out,
+                        int *auction_phases_out);
 
 /* Largest n that fram_sdsn_static accepts. */
 #define FRAM_SDSN_STATIC_MAX_N 4096

@@ -6,10 +6,10 @@ package never imports it, and it imports nothing from the product package.
 """
 from .fram_oracle import (DEFAULTS, DegenerateError, FramResult, InvalidInputError, SDSNResult,
                           accuracy, damped_update, fram, gamma, gradient, initial_assignment,
-                          lap_max, matching_error, objective, p1, p2, p3, prescale, sdsn,
-                          validate)
+                          lap_max, matching_error, node_affinity, objective, p1, p2, p3,
+                          prescale, sdsn, validate)
 
 __all__ = ["DEFAULTS", "DegenerateError", "FramResult", "InvalidInputError", "SDSNResult",
            "accuracy", "damped_update", "fram", "gamma", "gradient", "initial_assignment",
-           "lap_max", "matching_error", "objective", "p1", "p2", "p3", "prescale", "sdsn",
+           "lap_max", "matching_error", "node_affinity", "objective", "p1", "p2", "p3", "prescale", "sdsn",
            "validate"]

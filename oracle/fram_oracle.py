@@ -87,6 +87,19 @@ def initial_assignment(n, has_K):
 
 
 # --------------------------------------------------------------------------
+# Eq. 1 node term <N, F F~^T> (Sec. 3 "Matching matrix"; its gradient is the
+# lambda F F~^T of eq. 3): K[i, j] = <F[i], F~[j]>, node i of G against node
+# j of G~.
+# --------------------------------------------------------------------------
+def node_affinity(F, Ft):
+    F = np.asarray(F, dtype=np.float64)
+    Ft = np.asarray(Ft, dtype=np.float64)
+    if F.ndim != 2 or Ft.ndim != 2 or F.shape != Ft.shape or F.shape[0] < 1 or F.shape[1] < 1:
+        raise InvalidInputError("F and F~ must both be n x d with n, d >= 1")
+    return F @ Ft.T
+
+
+# --------------------------------------------------------------------------
 # Eq. 3 / Alg. 1 step 5: the QAP gradient  X = A N A~ + lambda K.
 # --------------------------------------------------------------------------
 def gradient(A, N, B, K=None, lam=1.0):

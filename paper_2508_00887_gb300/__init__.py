@@ -47,7 +47,7 @@ class FramParams(C.Structure):
 class FramInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("total_sweeps", C.c_int), ("polish_sweeps", C.c_int),
                 ("sdsn_converged_last", C.c_int), ("lap_augmentations", C.c_int),
-                ("reserved", C.c_int), ("delta", C.c_double), ("gamma", C.c_double),
+                ("lap_auction_phases", C.c_int), ("delta", C.c_double), ("gamma", C.c_double),
                 ("objective", C.c_double), ("match_error", C.c_double),
                 ("assignment_value", C.c_double), ("ms_total", C.c_double),
                 ("ms_gemm", C.c_double), ("ms_sdsn", C.c_double), ("ms_polish", C.c_double),
@@ -91,10 +91,11 @@ def load(path: str | None = None):
         "fram_submit": (i, [_P, i, _P, _P, C.POINTER(FramParams), C.POINTER(u64)]),
         "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
+        "fram_node_affinity": (i, [_P, i, i, _P, _P, _P]),
         "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
-        "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d)]),
+        "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d), C.POINTER(i)]),
         "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
                                  sz]),
     }
@@ -111,7 +112,7 @@ def exported_symbols():
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
             "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
+            "fram_poll", "fram_node_affinity", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
 
@@ -233,6 +234,13 @@ def fram_poll(ctx, ticket, X_out=None, perm_out=None, wait_ms=0, check=True):
     return st, info
 
 
+def fram_node_affinity(ctx, n, d, F, Ft, K, check=True):
+    st = load().fram_node_affinity(ctx, n, d, _addr(F), _addr(Ft), _addr(K))
+    if check:
+        _check(ctx, st)
+    return st
+
+
 def fram_gradient(ctx, n, A, N, B, X, K=None, lam=1.0, check=True):
     st = load().fram_gradient(ctx, n, _addr(A), _addr(N), _addr(B), _addr(K), lam, _addr(X))
     if check:
@@ -288,9 +296,10 @@ def fram_sdsn_grouped(ctx, ns, Xs, Ds, theta, gamma_tol=1e-14, max_sweeps=200, c
     return st, list(sw), list(g)
 
 
-def fram_assign(ctx, n, W, perm, check=True):
+def fram_assign(ctx, n, W, perm, check=True, with_phases=False):
     v = C.c_double()
-    st = load().fram_assign(ctx, n, _addr(W), _addr(perm, "int32"), C.byref(v))
+    ph = C.c_int()
+    st = load().fram_assign(ctx, n, _addr(W), _addr(perm, "int32"), C.byref(v), C.byref(ph))
     if check:
         _check(ctx, st)
-    return st, v.value
+    return (st, v.value, ph.value) if with_phases else (st, v.value)

@@ -334,7 +334,8 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
   }
 
   // Alg. 1 step 10 and eq. 1 on the unscaled inputs.
-  FR_LAUNCH(launch_lap(w.N, ld, n, w.perm, &w.scal->lap, w.lap_ws, c->stream), "lap kernels");
+  FR_LAUNCH(launch_lap(w.N, ld, n, w.perm, &w.scal->lap, w.lap_ws, c->num_sms, c->wait_limit_ns,
+                       c->stream), "lap kernels");
   FR_LAUNCH(launch_objective(A0, B0, K0, p.lambda, n, w.perm, &w.scal->obj, w.partials,
                              &w.scal->ticket_obj, c->stream),
             "objective kernel");
@@ -357,6 +358,7 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   inf.lap_augmentations = w.hscal->lap.augmented;
+  inf.lap_auction_phases = w.hscal->lap.auction_phases;
   inf.assignment_value = w.hscal->lap.value;
   inf.objective = w.hscal->obj.objective;
   inf.match_error = w.hscal->obj.match_error;
@@ -498,6 +500,21 @@ fram_status fram_solve(fram_ctx* c, int n, const double* A, const double* B, con
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "set device");
   std::lock_guard<std::mutex> lk(c->mu);
   return solve_one(c, n, A, B, K, p, X_out, perm_out, info);
+}
+
+fram_status fram_node_affinity(fram_ctx* c, int n, int d, const double* F, const double* Ft,
+                               double* K) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || d < 1 || !F || !Ft || !K || !is_device_ptr(F) || !is_device_ptr(Ft) ||
+      !is_device_ptr(K)) {
+    set_err(c, "fram_node_affinity: n, d >= 1 and device pointers F, Ft, K are required");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_LAUNCH(launch_node_affinity(F, Ft, n, d, K, c->stream), "node affinity kernel");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  return FRAM_OK;
 }
 
 fram_status fram_gradient(fram_ctx* c, int n, const double* A, const double* Nm, const double* B,
@@ -686,7 +703,8 @@ fram_status fram_sdsn_grouped(fram_ctx* c, int count, const int* n, const double
   return FRAM_OK;
 }
 
-fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, double* value_out) {
+fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, double* value_out,
+                        int* auction_phases_out) {
   if (!c) return FRAM_ERR_INVALID;
   c->last_error.clear();
   if (n < 1 || !W || !perm || !is_device_ptr(W) || !is_device_ptr(perm)) {
@@ -696,7 +714,8 @@ fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, doub
   std::lock_guard<std::mutex> lk(c->mu);
   FR_TRY(ensure_workspace(c, n));
   Workspace& w = c->ws;
-  FR_LAUNCH(launch_lap(W, n, n, perm, &w.scal->lap, w.lap_ws, c->stream), "lap kernels");
+  FR_LAUNCH(launch_lap(W, n, n, perm, &w.scal->lap, w.lap_ws, c->num_sms, c->wait_limit_ns,
+                       c->stream), "lap kernels");
   FR_CUDA(cudaMemcpyAsync(&w.hscal->lap, &w.scal->lap, sizeof(LapStats), cudaMemcpyDeviceToHost,
                           c->stream),
           "readback");
@@ -706,6 +725,7 @@ fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, doub
     return FRAM_ERR_TIMEOUT;
   }
   if (value_out) *value_out = w.hscal->lap.value;
+  if (auction_phases_out) *auction_phases_out = w.hscal->lap.auction_phases;
   return FRAM_OK;
 }
 

@@ -795,6 +795,7 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
       f.outer_iters = bi.outer_iters;
       f.total_sweeps = bi.total_sweeps;
       f.lap_augmentations = bi.lap_aug;
+      f.lap_auction_phases = -1;
       f.delta = bi.delta;
       f.gamma = bi.gamma;
       f.sdsn_converged_last = bi.gamma <= a.gamma_tol ? 1 : 0;

@@ -279,6 +279,52 @@ __global__ void __launch_bounds__(kRowThreads) objective_kernel(
   }
 }
 
+// Node-attribute affinity K = F Ft^T (eq. 1's node term, eq. 3's lambda F F~^T)
+// for n x d row-major F, Ft and an n x n row-major K: 64 x 64 output tiles,
+// 4 x 4 per thread, d staged through shared memory in chunks of 16 with zero
+// fill past n and d.  Each entry sums over k in increasing order.
+constexpr int NT_T = 64, NT_K = 16;
+
+__global__ void __launch_bounds__(256) nt_gemm_kernel(const double* __restrict__ F,
+                                                      const double* __restrict__ Ft, int n, int d,
+                                                      double* __restrict__ K) {
+  __shared__ double sa[NT_K][NT_T + 1];
+  __shared__ double sb[NT_K][NT_T + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.y * NT_T, c0 = blockIdx.x * NT_T;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < d; k0 += NT_K) {
+    for (int e = threadIdx.x; e < NT_T * NT_K; e += 256) {
+      const int r = e / NT_K, k = e % NT_K;
+      const bool kin = k0 + k < d;
+      sa[k][r] = (r0 + r < n && kin) ? F[(size_t)(r0 + r) * d + k0 + k] : 0.0;
+      sb[k][r] = (c0 + r < n && kin) ? Ft[(size_t)(c0 + r) * d + k0 + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NT_K; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = sa[k][ty + 16 * q];
+        b[q] = sb[k][tx + 16 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = fma(a[q], b[p], acc[q][p]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int r = r0 + ty + 16 * q, c = c0 + tx + 16 * p;
+      if (r < n && c < n) K[(size_t)r * n + c] = acc[q][p];
+    }
+}
+
 __global__ void max_kernel(const double* __restrict__ X, int ldx, int n, unsigned long long* out) {
   __shared__ double red[kRowThreads / 32];
   double m = -INFINITY;
@@ -323,6 +369,13 @@ int launch_dgemm(const double* A, const double* B, double* C, int ld, int n, con
   if (ld % GT != 0) return -1;
   dim3 grid(ld / GT, ld / GT);
   dgemm_kernel<<<grid, 256, 0, s>>>(A, B, C, ld, n, K, lam, cmax_key);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_node_affinity(const double* F, const double* Ft, int n, int d, double* K,
+                         cudaStream_t s) {
+  const int tiles = (n + NT_T - 1) / NT_T;
+  nt_gemm_kernel<<<dim3(tiles, tiles), 256, 0, s>>>(F, Ft, n, d, K);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -141,8 +141,10 @@ struct IterStats {
 };
 
 struct LapStats {
-  int augmented;
-  int status;
+  int augmented;       // augmenting paths of the exact completion
+  int status;          // 0 ok, 1 the search did not terminate
+  int auction_phases;  // epsilon-scaling phases completed, -1 if the auction did not run
+  int pad;
   double value;
 };
 
@@ -169,6 +171,8 @@ int launch_scale(const double* src, int n, double inv, bool divide, double* dst,
 int launch_fill_assignment(double* N, int n, int ld, double value, cudaStream_t s);
 int launch_dgemm(const double* A, const double* B, double* C, int ld, int n, const double* K,
                  double lam, unsigned long long* cmax_bits, cudaStream_t s);
+int launch_node_affinity(const double* F, const double* Ft, int n, int d, double* K,
+                         cudaStream_t s);
 int launch_max(const double* X, int ldx, int n, unsigned long long* key, cudaStream_t s);
 
 struct SdsnLaunch {
@@ -204,7 +208,7 @@ int launch_update(double* N, int ldn, const double* D, int ldd, int n, double al
 size_t update_partials_elems(int n);
 
 int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
-               cudaStream_t s);
+               int num_sms, uint64_t limit_ns, cudaStream_t s);
 size_t lap_workspace_bytes(int n);
 
 int launch_wait_selftest(GridBarrier* bar, int* status, int blocks, uint64_t limit_ns,

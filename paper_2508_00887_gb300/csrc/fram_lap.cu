@@ -1,17 +1,28 @@
 // Discretisation (eq. 2 / Alg. 1 step 10 of arXiv 2508.00887):
 //   perm = argmax_{P in Pi_n} <P, W>   (= argmin ||P - W||_F over permutations)
 //
-// Two kernels.
 //  1. Row argmax, one warp per row (ties -> lowest column).  If the row
 //     argmaxes already form a permutation it is optimal: the sum of row
 //     maxima bounds every assignment from above.  This is the common case
 //     once FRAM has converged, because N is then close to a permutation.
-//  2. One CTA completes the assignment exactly with the Hungarian method in
-//     its shortest-augmenting-path form (Kuhn 1955 with row/column
-//     potentials), warm-started from the conflict-free part of step 1:
-//     u_i = -max_j W_ij, v_j = 0 is dual feasible for cost -W and tight on
-//     every argmax edge.  Each Dijkstra step scans all columns in parallel
-//     and picks the closest unvisited column with a block-wide argmin.
+//  2. Exact completion from that start (step 4) with a budget of 64 n
+//     Dijkstra steps.  Almost every FRAM output finishes here.
+//  3. A nearly flat W (every row within a hair of uniform) can need far more
+//     steps from the argmax start.  Past the budget, a forward auction with
+//     epsilon-scaling (Bertsekas 1988) computes near-optimal column prices p
+//     in one cooperative launch and the completion restarts from them.  It runs in the
+//     asynchronous Gauss-Seidel form: each CTA bids for its own rows with one
+//     64-bit atomicMax on a (quantised price, row) key, and a row it outbids
+//     is its to place next, so a chain of displacements costs one bid each
+//     and no CTA waits on another inside a phase.  Prices only rise, so a bid
+//     computed from stale prices is a lower bid and epsilon-complementary
+//     slackness still holds for the winner.
+//  4. Exact completion.  With column potentials v (0 after step 1, -p after
+//     step 3) a pair is kept only if its column minimises c_ij - v_j for the
+//     cost c = -W; one CTA then places the other rows by shortest augmenting
+//     paths (the Hungarian method of Kuhn 1955 in the Jonker-Volgenant
+//     form).  The auction only shortens these paths; the result is exact
+//     either way.
 #include <math.h>
 
 #include "fram_internal.cuh"
@@ -21,18 +32,37 @@ namespace fram {
 namespace {
 
 constexpr int kLapThreads = 1024;
+constexpr int kOwnerBits = 20;
+constexpr unsigned long long kNoOwner = (1ull << kOwnerBits) - 1;  // n < 2^20 - 1
+constexpr int kQuantBits = 36;   // price quantum = (max W - min W) * 2^-36
+constexpr int kPriceBits = 44;   // quantised prices < 2^44 (256x the value range)
+constexpr int kPhases = 12;      // epsilon = range * 4^-phase, phase = 1..12
+
+struct LapCtl {
+  GridBarrier bar;
+  unsigned long long wmax_key;  // ordered keys of max / min over W
+  unsigned long long wmin_key;
+  double dq;                    // price quantum
+  int nfree;                    // rows whose argmax column is taken by a lower row
+  int phases;                   // auction phases completed
+  int status;                   // DEV_TIMEOUT if an auction wait expired
+  int need_auction;             // the first completion ran out of its step budget
+};
 
 struct LapWs {
   int* argc;       // [n] row argmax column
-  int* owner;      // [n] lowest row claiming column j (INT_MAX if none)
+  int* owner;      // [n] lowest row claiming column j as argmax (INT_MAX if none)
   int* colrow;     // [n] row matched to column j, -1 if free
   int* rowcol;     // [n] column matched to row i, -1 if free
-  int* way;        // [n] predecessor column on the search tree, -1 = root
-  int* used;       // [n]
+  int* way;        // [n] completion: row that reached column j
+  int* cand;       // [n] candidate column of row i from step 1 or 2, -1 if none
   double* rowmax;  // [n]
-  double* u;       // [n]
-  double* v;       // [n]
-  double* minv;    // [n]
+  double* u;       // [n] row potentials of the kept pairs
+  double* v;       // [n] column potentials
+  unsigned long long* key;   // [n] auction: (quantised price << 20) | owner row;
+                             //     completion label keys when they do not fit on chip
+  unsigned long long* tkey;  // [n] completion test keys when they do not fit on chip
+  LapCtl* ctl;
 };
 
 __host__ __device__ inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -41,30 +71,46 @@ __host__ __device__ inline LapWs carve(void* base, int n) {
   LapWs w;
   char* p = static_cast<char*>(base);
   const size_t ib = al256((size_t)n * sizeof(int)), db = al256((size_t)n * sizeof(double));
-  w.argc = reinterpret_cast<int*>(p); p += ib;
-  w.owner = reinterpret_cast<int*>(p); p += ib;
-  w.colrow = reinterpret_cast<int*>(p); p += ib;
-  w.rowcol = reinterpret_cast<int*>(p); p += ib;
-  w.way = reinterpret_cast<int*>(p); p += ib;
-  w.used = reinterpret_cast<int*>(p); p += ib;
-  w.rowmax = reinterpret_cast<double*>(p); p += db;
-  w.u = reinterpret_cast<double*>(p); p += db;
-  w.v = reinterpret_cast<double*>(p); p += db;
-  w.minv = reinterpret_cast<double*>(p); p += db;
+  int** ia[] = {&w.argc, &w.owner, &w.colrow, &w.rowcol, &w.way, &w.cand};
+  for (int** q : ia) {
+    *q = reinterpret_cast<int*>(p);
+    p += ib;
+  }
+  double** da[] = {&w.rowmax, &w.u, &w.v};
+  for (double** q : da) {
+    *q = reinterpret_cast<double*>(p);
+    p += db;
+  }
+  w.key = reinterpret_cast<unsigned long long*>(p);
+  p += db;
+  w.tkey = reinterpret_cast<unsigned long long*>(p);
+  p += db;
+  w.ctl = reinterpret_cast<LapCtl*>(p);
   return w;
 }
 
-__global__ void lap_init_owner_kernel(LapWs w, int n) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+__global__ void lap_init_kernel(LapWs w, int n) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     w.owner[j] = 0x7fffffff;
+    w.cand[j] = -1;
+    w.key[j] = kNoOwner;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    LapCtl c{};
+    c.wmax_key = 0ull;
+    c.wmin_key = ~0ull;
+    *w.ctl = c;
+  }
 }
 
+// Row max and argmax (ties -> lowest column), the lowest row claiming each
+// argmax column, and the range of W.
 __global__ void lap_rowmax_kernel(const double* __restrict__ W, int ldw, int n, LapWs w) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const double* row = W + (size_t)i * ldw;
-    double best = -INFINITY;
+    double best = -INFINITY, lo = INFINITY;
     int bj = 0x7fffffff;
     for (int j = lane; j < n; j += 32) {
       const double x = row[j];
@@ -72,6 +118,7 @@ __global__ void lap_rowmax_kernel(const double* __restrict__ W, int ldw, int n, 
         best = x;
         bj = j;
       }
+      lo = fmin(lo, x);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -81,150 +128,457 @@ __global__ void lap_rowmax_kernel(const double* __restrict__ W, int ldw, int n, 
         best = ob;
         bj = oj;
       }
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     }
     if (lane == 0) {
       if (bj == 0x7fffffff) bj = 0;
       w.argc[i] = bj;
       w.rowmax[i] = best;
       atomicMin(&w.owner[bj], i);
+      atomicMax(&w.ctl->wmax_key, ordered_key(best));
+      atomicMin(&w.ctl->wmin_key, ordered_key(lo));
     }
   }
 }
 
-// Block-wide argmin over (value, index), ties -> lowest index.  Result in
-// s_val/s_idx for every thread after the call.
-__device__ __forceinline__ void block_argmin(double v, int j, double* rv, int* rj, double* s_val,
-                                             int* s_idx) {
+// Number of rows that lose their argmax column to a lower row; price quantum.
+__global__ void lap_conflicts_kernel(LapWs w, int n) {
+  int cnt = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    cnt += w.owner[w.argc[i]] != i;
+  cnt = warp_sum(cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&w.ctl->nfree, cnt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double range = from_ordered_key(w.ctl->wmax_key) - from_ordered_key(w.ctl->wmin_key);
+    w.ctl->dq = (range > 0.0 && range < INFINITY) ? ldexp(range, -kQuantBits) : 0.0;
+  }
+}
+
+// The auction runs when the first completion ran out of budget and W has a
+// finite, nonzero range.
+__device__ __forceinline__ bool auction_on(const LapCtl* c) {
+  return ld_volatile_s32(&c->need_auction) && c->dq > 0.0;
+}
+
+// Top two values of W_ij - p_j with the argmax (ties -> lowest column) and
+// the key read for it.
+struct Top2 {
+  double v1, v2;
+  int j1;
+  unsigned long long k1;
+};
+
+__device__ __forceinline__ void top2_merge(Top2& a, double ov1, int oj1, unsigned long long ok1,
+                                           double ov2) {
+  if (ov1 > a.v1 || (ov1 == a.v1 && oj1 < a.j1)) {
+    a.v2 = fmax(a.v1, ov2);
+    a.v1 = ov1;
+    a.j1 = oj1;
+    a.k1 = ok1;
+  } else {
+    a.v2 = fmax(a.v2, ov1);
+  }
+}
+
+__device__ __forceinline__ void top2_warp(Top2& t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double a = __shfl_xor_sync(0xffffffffu, t.v1, o);
+    const int b = __shfl_xor_sync(0xffffffffu, t.j1, o);
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, t.k1, o);
+    const double d = __shfl_xor_sync(0xffffffffu, t.v2, o);
+    top2_merge(t, a, b, c, d);
+  }
+}
+
+constexpr int kAucMaxThreads = 1024;
+constexpr int kAucUnroll = 8;  // independent loads in flight per thread
+
+// One auction bid of row i, block-uniform result: 1 if it won a column (the
+// row it displaced, or -1, in *displaced), 0 if it lost the race for it
+// (retry), 2 if the auction must stop (no finite value, price range
+// exhausted, time limit passed, or another CTA stopped it).
+__device__ int auction_bid(const double* __restrict__ row, int i, int n, LapWs& w, double dq,
+                           long long eps_q, uint64_t t0, uint64_t limit_ns, int* displaced) {
+  __shared__ Top2 s_t[kAucMaxThreads / 32];
+  __shared__ int s_res, s_disp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  Top2 t{-INFINITY, -INFINITY, 0x7fffffff, 0ull};
+  for (int base = tid; base < n; base += kAucUnroll * nt) {
+    unsigned long long kv[kAucUnroll];
+    double wv[kAucUnroll];
+#pragma unroll
+    for (int u = 0; u < kAucUnroll; ++u) {
+      const int j = base + u * nt;
+      if (j < n) {
+        kv[u] = __ldcg(w.key + j);
+        wv[u] = row[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kAucUnroll; ++u) {
+      const int j = base + u * nt;
+      if (j < n) top2_merge(t, wv[u] - (double)(kv[u] >> kOwnerBits) * dq, j, kv[u], -INFINITY);
+    }
+  }
+  top2_warp(t);
+  if (lane == 0) s_t[warp] = t;
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 1; q < nt >> 5; ++q) top2_merge(t, s_t[q].v1, s_t[q].j1, s_t[q].k1, s_t[q].v2);
+    // Bid: the row's value for j1 drops to (second best - eps).
+    double d = (t.v1 - t.v2) / dq;  // >= 0; +inf when n == 1
+    if (!(d < 0x1p43)) d = 0x1p43;
+    const long long qn = (long long)(t.k1 >> kOwnerBits) + (long long)ceil(d) + eps_q;
+    int res = 0, disp = -1;
+    if (t.j1 >= n || !(t.v1 > -INFINITY) || qn >= (1ll << kPriceBits) ||
+        ld_volatile_s32(&w.ctl->bar.abort)) {
+      res = 2;  // no finite value, price range exhausted, or stopped elsewhere
+    } else {
+      const unsigned long long nk = ((unsigned long long)qn << kOwnerBits) | (unsigned)i;
+      const unsigned long long old = atomicMax(w.key + t.j1, nk);
+      if (old < nk) {
+        res = 1;
+        const unsigned long long prev = old & kNoOwner;
+        disp = prev == kNoOwner ? -1 : (int)prev;
+      }
+    }
+    if (res == 0 && globaltimer_ns() - t0 > limit_ns) res = 2;
+    if (res == 2) atomicExch(&w.ctl->bar.abort, 1);
+    s_res = res;
+    s_disp = disp;
+  }
+  __syncthreads();
+  const int r = s_res;
+  *displaced = s_disp;
+  __syncthreads();
+  return r;
+}
+
+// All epsilon-scaling phases in one cooperative launch.  A phase ends when
+// every CTA has placed its rows and every row they displaced; then every row
+// owns one column.  Stops early (leaving the rest to the exact completion)
+// on a wait, time or price limit.
+__global__ void __launch_bounds__(kAucMaxThreads) lap_auction_kernel(
+    const double* __restrict__ W, int ldw, int n, LapWs w, uint64_t limit_ns) {
+  if (!auction_on(w.ctl)) return;  // grid-uniform: set by earlier kernels
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  const double dq = w.ctl->dq;
+  unsigned gen = 0;
+  const uint64_t t0 = globaltimer_ns();
+  for (int phase = 1; phase <= kPhases; ++phase) {
+    const long long eps_q = 1ll << (kQuantBits - 2 * phase);
+    // Keep the prices, release every column.
+    for (int j = blockIdx.x * blockDim.x + tid; j < n; j += gridDim.x * blockDim.x)
+      w.key[j] = phase == 1 ? kNoOwner : (__ldcg(w.key + j) | kNoOwner);  // L2: atomics
+    if (!grid_sync(&w.ctl->bar, gridDim.x, gen, limit_ns, &w.ctl->status, &s_flag)) return;
+    for (int i0 = blockIdx.x; i0 < n; i0 += gridDim.x) {
+      int i = i0;
+      while (i >= 0) {
+        int disp;
+        const int r = auction_bid(W + (size_t)i * ldw, i, n, w, dq, eps_q, t0, limit_ns, &disp);
+        if (r == 2) return;  // abort raised: CTAs at a barrier leave too
+        if (r == 1) i = disp;
+      }
+    }
+    if (!grid_sync(&w.ctl->bar, gridDim.x, gen, limit_ns, &w.ctl->status, &s_flag)) return;
+    if (blockIdx.x == 0 && tid == 0) w.ctl->phases = phase;
+  }
+}
+
+// Candidate pairs and column potentials.  Pass 0: the conflict-free argmaxes
+// with v = 0.  Pass 1 (only after the budget ran out): the auction's pairs
+// and v = -p if it ran, else the argmaxes again.
+__global__ void lap_candidates_kernel(LapWs w, int n, int pass) {
+  if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;
+  const bool auction = pass == 1 && auction_on(w.ctl);
+  const double dq = w.ctl->dq;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    w.colrow[j] = -1;
+    if (auction) {
+      const unsigned long long k = w.key[j];
+      w.v[j] = -(double)(k >> kOwnerBits) * dq;
+      const unsigned long long r = k & kNoOwner;
+      if (r != kNoOwner) w.cand[r] = j;
+    } else {
+      w.v[j] = 0.0;
+      const int r = w.owner[j];
+      if (r != 0x7fffffff) w.cand[r] = j;
+    }
+  }
+}
+
+// u_i = -max_j (W_ij + v_j); keep the candidate pair of row i if it is
+// tight, and clear the candidate for the next pass.
+__global__ void lap_duals_kernel(const double* __restrict__ W, int ldw, int n, LapWs w,
+                                 int pass) {
+  if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const double* row = W + (size_t)i * ldw;
+    double best = -INFINITY;
+    for (int j = lane; j < n; j += 32) best = fmax(best, row[j] + w.v[j]);
+    best = warp_max(best);
+    if (lane == 0) {
+      const int j = w.cand[i];
+      w.cand[i] = -1;
+      w.u[i] = -best;
+      if (j >= 0 && row[j] + w.v[j] == best) {
+        w.rowcol[i] = j;
+        w.colrow[j] = i;
+      } else {
+        w.rowcol[i] = -1;
+      }
+    }
+  }
+}
+
+// Shared memory for the completion state: label keys, test keys and
+// potentials (8 bytes each) and colrow (4 bytes) per column.
+constexpr size_t kSolveSmemCap = 225 * 1024;
+
+__host__ __device__ inline size_t solve_smem_bytes(int n) {
+  return al256((size_t)n * 8) * 3 + al256((size_t)n * 4);
+}
+
+// Order-preserving map of a double onto uint64 with integer operations only
+// (FP64 instructions are scarce on this GPU; compares run on the ALU).
+__device__ __forceinline__ unsigned long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return (unsigned long long)(b ^ ((b >> 63) | (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+  const long long b = (long long)k;
+  return __longlong_as_double(b ^ ((~b >> 63) | (long long)0x8000000000000000ull));
+}
+
+constexpr unsigned long long kVisited = ~0ull;  // label key of a popped column
+
+// Block-wide argmin over (key, k) pairs, lexicographic, integer compares.
+// The result is in *s_key / *s_k for every thread after the call.
+__device__ __forceinline__ void block_argmin_key(unsigned long long key, int k,
+                                                 unsigned long long* rk, int* rkk,
+                                                 unsigned long long* s_key, int* s_k) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int oj = __shfl_xor_sync(0xffffffffu, j, o);
-    if (ov < v || (ov == v && oj < j)) {
-      v = ov;
-      j = oj;
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+    const int ok2 = __shfl_xor_sync(0xffffffffu, k, o);
+    if (ok < key || (ok == key && ok2 < k)) {
+      key = ok;
+      k = ok2;
     }
   }
   if (lane == 0) {
-    rv[warp] = v;
-    rj[warp] = j;
+    rk[warp] = key;
+    rkk[warp] = k;
   }
   __syncthreads();
   if (warp == 0) {
-    v = lane < (kLapThreads / 32) ? rv[lane] : INFINITY;
-    j = lane < (kLapThreads / 32) ? rj[lane] : 0x7fffffff;
+    key = lane < (kLapThreads / 32) ? rk[lane] : kVisited;
+    k = lane < (kLapThreads / 32) ? rkk[lane] : 0x7fffffff;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, j, o);
-      if (ov < v || (ov == v && oj < j)) {
-        v = ov;
-        j = oj;
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int ok2 = __shfl_xor_sync(0xffffffffu, k, o);
+      if (ok < key || (ok == key && ok2 < k)) {
+        key = ok;
+        k = ok2;
       }
     }
     if (lane == 0) {
-      *s_val = v;
-      *s_idx = j;
+      *s_key = key;
+      *s_k = k;
     }
   }
   __syncthreads();
 }
 
+// Exact completion in the Jonker-Volgenant form of the shortest augmenting
+// path (cost c = -W, column potentials v only; an assigned row i satisfies
+// c_i,col(i) - v_col(i) = min_j (c_ij - v_j)).  For a free row f the
+// Dijkstra labels start at d_j = c_fj - v_j; popping column j1 at distance
+// mu reaches row i = colrow[j1], whose relaxation is
+//   d_j = min(d_j, c_ij - v_j - h),   h = c_i,j1 - v_j1 - mu.
+// Each column also keeps t_j = -(v_j + d_j), so the test d_j > c_ij - v_j - h
+// reads W_ij + h > t_j: one FP64 add per column and step, the comparison on
+// order-preserving integer keys.  Among equal labels a free column is popped
+// first.  At a free column every popped column gets v_j += d_j - mu (its
+// label at the pop is kept in place of t_j) and the path is flipped.
+// Column j's state belongs to thread j % 1024, so a step is one fused
+// relax-and-argmin pass whose row loads are issued together.  The state
+// sits in shared memory when it fits, else in the workspace.  Pass 0 stops
+// after `budget` steps (0 = no limit) and asks for the auction; pass 1 runs
+// only then.
+constexpr int kSolveUnroll = 8;
+
 __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double* __restrict__ W,
                                                                    int ldw, int n, LapWs w,
+                                                                   int pass, long long budget,
+                                                                   int use_smem,
                                                                    int32_t* __restrict__ perm,
                                                                    LapStats* st) {
-  __shared__ double rv[kLapThreads / 32];
-  __shared__ int rj[kLapThreads / 32];
-  __shared__ double s_val;
-  __shared__ int s_idx;
+  if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;
+  extern __shared__ __align__(16) unsigned char lap_sm[];
+  __shared__ unsigned long long rk[kLapThreads / 32];
+  __shared__ int rkk[kLapThreads / 32];
+  __shared__ unsigned long long s_key;
+  __shared__ int s_k;
+  __shared__ double s_h;
   __shared__ int s_aug;
   const int tid = threadIdx.x;
-  for (int j = tid; j < n; j += kLapThreads) {
-    w.colrow[j] = -1;
-    w.v[j] = 0.0;
-  }
-  for (int i = tid; i < n; i += kLapThreads) w.rowcol[i] = -1;
-  __syncthreads();
-  for (int i = tid; i < n; i += kLapThreads) {
-    const int j = w.argc[i];
-    w.u[i] = -w.rowmax[i];
-    if (w.owner[j] == i) {
-      w.colrow[j] = i;
-      w.rowcol[i] = j;
+  unsigned long long *dkey, *tkey;
+  double* v;
+  int* colrow;
+  if (use_smem) {
+    unsigned char* p = lap_sm;
+    dkey = reinterpret_cast<unsigned long long*>(p);
+    p += al256((size_t)n * 8);
+    tkey = reinterpret_cast<unsigned long long*>(p);
+    p += al256((size_t)n * 8);
+    v = reinterpret_cast<double*>(p);
+    p += al256((size_t)n * 8);
+    colrow = reinterpret_cast<int*>(p);
+    for (int j = tid; j < n; j += kLapThreads) {
+      v[j] = w.v[j];
+      colrow[j] = w.colrow[j];
     }
+  } else {
+    dkey = w.key;
+    tkey = w.tkey;
+    v = w.v;
+    colrow = w.colrow;
   }
+  int* pred = w.way;
   if (tid == 0) {
     s_aug = 0;
     st->status = 0;
+    st->auction_phases = pass == 1 && auction_on(w.ctl) ? w.ctl->phases : -1;
   }
   __syncthreads();
 
-  for (int root = 0; root < n; ++root) {
-    if (w.rowcol[root] != -1) continue;  // uniform: read after a barrier
-    for (int j = tid; j < n; j += kLapThreads) {
-      w.minv[j] = INFINITY;
-      w.used[j] = 0;
-      w.way[j] = -1;
-    }
-    __syncthreads();
-    int i0 = root, j0 = -1, steps = 0;
-    while (true) {
-      double best = INFINITY;
-      int bj = 0x7fffffff;
-      const double ui = w.u[i0];
-      const double* row = W + (size_t)i0 * ldw;
-      for (int j = tid; j < n; j += kLapThreads) {
-        if (w.used[j]) continue;
-        const double cur = -row[j] - ui - w.v[j];
-        double mv = w.minv[j];
-        if (cur < mv) {
-          mv = cur;
-          w.minv[j] = cur;
-          w.way[j] = j0;
-        }
-        if (mv < best) {
-          best = mv;
-          bj = j;
+  long long total = 0;  // Dijkstra steps of this pass (the same in every thread)
+  for (int f = 0; f < n; ++f) {
+    if (w.rowcol[f] != -1) continue;  // uniform: read after a barrier
+    const double* rowf = W + (size_t)f * ldw;
+    unsigned long long best = kVisited;
+    int bk = 0x7fffffff;  // argmin tie key: j, plus n if column j is assigned
+    for (int base = tid; base < n; base += kSolveUnroll * kLapThreads) {
+      double wv[kSolveUnroll];
+#pragma unroll
+      for (int u = 0; u < kSolveUnroll; ++u) {
+        const int j = base + u * kLapThreads;
+        if (j < n) wv[u] = rowf[j];
+      }
+#pragma unroll
+      for (int u = 0; u < kSolveUnroll; ++u) {
+        const int j = base + u * kLapThreads;
+        if (j >= n) continue;
+        const unsigned long long dk = okey(-(wv[u] + v[j]));
+        dkey[j] = dk;
+        tkey[j] = okey(wv[u]);
+        pred[j] = f;
+        const int k = colrow[j] == -1 ? j : j + n;
+        if (dk < best || (dk == best && k < bk)) {
+          best = dk;
+          bk = k;
         }
       }
-      block_argmin(best, bj, rv, rj, &s_val, &s_idx);
-      const double delta = s_val;
-      const int j1 = s_idx;
-      if (j1 < 0 || j1 >= n) {  // cannot happen for finite W; stop safely
+    }
+    block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+    double mu = okey_value(s_key);
+    int key = s_k;
+    int steps = 0;
+    int j1;
+    while (true) {
+      if (key < 0 || key >= 2 * n || s_key == kVisited) {  // no finite label left
         if (tid == 0) st->status = 1;
         return;
       }
-      for (int j = tid; j < n; j += kLapThreads) {
-        if (w.used[j]) {
-          w.v[j] -= delta;
-          w.u[w.colrow[j]] += delta;
-        } else {
-          w.minv[j] -= delta;
+      j1 = key >= n ? key - n : key;
+      if (j1 % kLapThreads == tid) {  // pop: keep the label where t_j was
+        tkey[j1] = (unsigned long long)__double_as_longlong(mu);
+        dkey[j1] = kVisited;
+      }
+      const int i = colrow[j1];
+      if (i == -1) break;
+      const double* rowi = W + (size_t)i * ldw;
+      double wv[kSolveUnroll];
+      // Issue this thread's row loads before h is known.
+      const bool pre = n <= kSolveUnroll * kLapThreads;
+      if (pre) {
+#pragma unroll
+        for (int u = 0; u < kSolveUnroll; ++u) {
+          const int j = tid + u * kLapThreads;
+          if (j < n) wv[u] = rowi[j];
         }
       }
-      if (tid == 0) {
-        w.u[root] += delta;
-        w.used[j1] = 1;
-      }
+      if (tid == 0) s_h = -(rowi[j1] + v[j1]) - mu;
       __syncthreads();
-      j0 = j1;
-      const int nxt = w.colrow[j1];
-      if (nxt == -1) break;
-      i0 = nxt;
+      const double h = s_h;
+      best = kVisited;
+      bk = 0x7fffffff;
+      for (int base = tid; base < n; base += kSolveUnroll * kLapThreads) {
+        if (!pre || base != tid) {
+#pragma unroll
+          for (int u = 0; u < kSolveUnroll; ++u) {
+            const int j = base + u * kLapThreads;
+            if (j < n) wv[u] = rowi[j];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveUnroll; ++u) {
+          const int j = base + u * kLapThreads;
+          if (j >= n) continue;
+          unsigned long long dk = dkey[j];
+          if (dk == kVisited) continue;
+          const double x = wv[u] + h;
+          const unsigned long long xk = okey(x);
+          if (xk > tkey[j]) {  // W_ij + h > t_j: a shorter path to column j
+            tkey[j] = xk;
+            const unsigned long long nk = okey(-(x + v[j]));
+            if (nk < dk) {
+              dk = nk;
+              dkey[j] = nk;
+              pred[j] = i;
+            }
+          }
+          const int k = colrow[j] == -1 ? j : j + n;
+          if (dk < best || (dk == best && k < bk)) {
+            best = dk;
+            bk = k;
+          }
+        }
+      }
+      block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+      mu = okey_value(s_key);
+      key = s_k;
+      ++total;
       if (++steps > n) {
         if (tid == 0) st->status = 1;
         return;
       }
+      if (budget > 0 && total > budget) {
+        if (tid == 0) atomicExch(&w.ctl->need_auction, 1);
+        return;
+      }
     }
+    // Potentials of the popped columns (label at the pop is in tkey), then
+    // flip the path (j1 is free).
+    for (int j = tid; j < n; j += kLapThreads)
+      if (dkey[j] == kVisited) v[j] += __longlong_as_double((long long)tkey[j]) - mu;
+    __syncthreads();
     if (tid == 0) {
-      int j = j0;
-      while (j != -1) {
-        const int jp = w.way[j];
-        const int r = (jp == -1) ? root : w.colrow[jp];
-        w.colrow[j] = r;
+      int j = j1;
+      while (true) {
+        const int r = pred[j];
+        const int prev = w.rowcol[r];
+        colrow[j] = r;
         w.rowcol[r] = j;
-        j = jp;
+        if (r == f) break;
+        j = prev;
       }
       ++s_aug;
     }
@@ -238,11 +592,12 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
     val += W[(size_t)i * ldw + j];
   }
   val = warp_sum(val);
+  __shared__ double rsum[kLapThreads / 32];
   const int lane = tid & 31, warp = tid >> 5;
-  if (lane == 0) rv[warp] = val;
+  if (lane == 0) rsum[warp] = val;
   __syncthreads();
   if (warp == 0) {
-    double t = rv[lane];
+    double t = rsum[lane];
     t = warp_sum(t);
     if (lane == 0) {
       st->value = t;
@@ -251,23 +606,78 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
   }
 }
 
+// Auction CTA size: about 8 columns per thread, 32..1024 threads.
+int auction_threads(int n) {
+  int t = 32;
+  while (t < kAucMaxThreads && t * kAucUnroll < n) t *= 2;
+  return t;
+}
+
+int launch_auction(const double* W, int ldw, int n, LapWs w, int num_sms, uint64_t limit_ns,
+                   cudaStream_t s) {
+  static int per_sm[11] = {};  // by log2(threads)
+  const int t = auction_threads(n);
+  const int lg = 31 - __builtin_clz((unsigned)t);
+  if (per_sm[lg] == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lap_auction_kernel, t, 0) != cudaSuccess)
+      return -1;
+    per_sm[lg] = v > 0 ? v : -1;
+  }
+  if (per_sm[lg] < 0 || num_sms < 1) return -1;
+  int blocks = per_sm[lg] * num_sms;
+  if (blocks > n) blocks = n;
+  void* args[] = {(void*)&W, (void*)&ldw, (void*)&n, (void*)&w, (void*)&limit_ns};
+  if (cudaLaunchCooperativeKernel((const void*)lap_auction_kernel, dim3(blocks), dim3(t), args,
+                                  0, s) != cudaSuccess)
+    return -1;
+  return 1;
+}
+
 }  // namespace
 
 size_t lap_workspace_bytes(int n) {
-  return 6 * al256((size_t)n * sizeof(int)) + 4 * al256((size_t)n * sizeof(double));
+  return 6 * al256((size_t)n * sizeof(int)) + 5 * al256((size_t)n * sizeof(double)) +
+         al256(sizeof(LapCtl));
 }
 
 int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
-               cudaStream_t s) {
+               int num_sms, uint64_t limit_ns, cudaStream_t s) {
   LapWs w = carve(ws, n);
+  // The auction key holds a 20-bit row index; beyond that the first
+  // completion runs without a budget.
+  const bool can_auction = n < (int)kNoOwner;
+  const long long budget = can_auction ? 64ll * n : 0;
   int blocks = (n + 255) / 256;
   if (blocks > 1184) blocks = 1184;
-  lap_init_owner_kernel<<<blocks, 256, 0, s>>>(w, n);
   int rblocks = (n * 32 + 255) / 256;
   if (rblocks > 2368) rblocks = 2368;
+  const size_t sm = solve_smem_bytes(n);
+  const int use_smem = sm <= kSolveSmemCap;
+  static bool attr_set = false;
+  if (use_smem && !attr_set) {
+    if (cudaFuncSetAttribute(lap_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSolveSmemCap) != cudaSuccess)
+      return -1;
+    attr_set = true;
+  }
+  const size_t dsm = use_smem ? sm : 0;
+  lap_init_kernel<<<blocks, 256, 0, s>>>(w, n);
   lap_rowmax_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w);
-  lap_solve_kernel<<<1, kLapThreads, 0, s>>>(W, ldw, n, w, perm, st);
-  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+  lap_conflicts_kernel<<<blocks, 256, 0, s>>>(w, n);
+  lap_candidates_kernel<<<blocks, 256, 0, s>>>(w, n, 0);
+  lap_duals_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w, 0);
+  lap_solve_kernel<<<1, kLapThreads, dsm, s>>>(W, ldw, n, w, 0, budget, use_smem, perm, st);
+  int launches = 6;
+  if (can_auction) {
+    // Each of these returns at once unless the first completion ran out.
+    if (launch_auction(W, ldw, n, w, num_sms, limit_ns, s) < 0) return -1;
+    lap_candidates_kernel<<<blocks, 256, 0, s>>>(w, n, 1);
+    lap_duals_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w, 1);
+    lap_solve_kernel<<<1, kLapThreads, dsm, s>>>(W, ldw, n, w, 1, 0, use_smem, perm, st);
+    launches += 4;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
 }
 
 }  // namespace fram

@@ -411,7 +411,8 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       SlotStats* st = &S.dstats[r->sid];
       r->Nres.resize((size_t)r->n * r->n);
       r->permres.resize(r->n);
-      SV_OK(launch_lap(r->N, r->ld, r->n, r->perm, &st->lap, r->lap_ws, s));
+      SV_OK(launch_lap(r->N, r->ld, r->n, r->perm, &st->lap, r->lap_ws, c->num_sms,
+                       c->wait_limit_ns, s));
       SV_OK(launch_objective(r->A0, r->B0, nullptr, r->p.lambda, r->n, r->perm, &st->obj, r->upart,
                              &st->ticket_obj, s));
       cudaMemcpy2DAsync(r->Nres.data(), (size_t)r->n * 8, r->N, (size_t)r->ld * 8, (size_t)r->n * 8,
@@ -427,6 +428,7 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       }
       const SlotStats& st = S.hstats[r->sid];
       r->info.lap_augmentations = st.lap.augmented;
+      r->info.lap_auction_phases = st.lap.auction_phases;
       r->info.assignment_value = st.lap.value;
       r->info.objective = st.obj.objective;
       r->info.match_error = st.obj.match_error;

@@ -73,7 +73,7 @@ int main(void) {{
       "max_sweeps", "max_polish", "precision", "init", "reserved"]),
     ("fram_info", fr.FramInfo,
      ["outer_iters", "total_sweeps", "polish_sweeps", "sdsn_converged_last", "lap_augmentations",
-      "reserved", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total",
+      "lap_auction_phases", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total",
       "ms_gemm", "ms_sdsn", "ms_polish", "ms_update"]),
 ])
 def test_struct_layouts_match_header(cname, pystruct, cfields):

@@ -149,6 +149,51 @@ def test_assign_ties_valid(torch_cuda, ctx):
     assert abs(val - n) < 1e-12
 
 
+@pytest.mark.parametrize("levels", [2, 4])
+def test_assign_integer_ties_optimal_value(torch_cuda, ctx, levels):
+    # Few distinct values: the row reduction meets tied minima at almost every
+    # step.  The optimum value is unique even where the permutation is not.
+    torch = torch_cuda
+    n = 300
+    W = np.random.default_rng(levels).integers(0, levels, (n, n)).astype(np.float64)
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    _, val = fr.fram_assign(ctx, n, dev(torch, W), perm)
+    p = perm.cpu().numpy().astype(np.int64)
+    ref = o.lap_max(W)
+    assert sorted(p.tolist()) == list(range(n))
+    assert W[np.arange(n), p].sum() == W[np.arange(n), ref].sum()
+    assert val == W[np.arange(n), ref].sum()
+
+
+def test_assign_constant_matrix(torch_cuda, ctx):
+    torch = torch_cuda
+    n = 500
+    W = np.full((n, n), 0.25)
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    _, val = fr.fram_assign(ctx, n, dev(torch, W), perm)
+    assert sorted(perm.cpu().numpy().tolist()) == list(range(n))
+    assert val == 0.25 * n
+
+
+def test_assign_diffuse_doubly_stochastic(torch_cuda, ctx):
+    # A near-uniform doubly stochastic matrix, as FRAM produces at small theta
+    # on large pairs: almost every argmax conflicts.
+    torch = torch_cuda
+    n = 1500
+    rng = np.random.default_rng(11)
+    W = 1.0 + 1e-3 * rng.random((n, n))
+    for _ in range(20):
+        W /= W.sum(1, keepdims=True)
+        W /= W.sum(0, keepdims=True)
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    _, val, phases = fr.fram_assign(ctx, n, dev(torch, W), perm, with_phases=True)
+    p = perm.cpu().numpy().astype(np.int64)
+    ref = o.lap_max(W)
+    assert abs(val - W[np.arange(n), ref].sum()) <= 1e-12 * n
+    assert np.array_equal(p, ref)
+    assert phases == 12      # the argmax start ran out of its step budget
+
+
 # ------------------------------------------------------------ full solve
 def solve_gpu(torch, ctx, g, params=None, K=None, host=False):
     n = g.n
@@ -204,6 +249,17 @@ def test_solve_gaussian_dense_matches_oracle(torch_cuda, ctx):
     ref = o.fram(g.A, g.B, theta=g.theta)
     X, P, info = solve_gpu(torch_cuda, ctx, g)
     check_against_oracle(g, X, P, info, ref)
+
+
+def test_solve_gaussian_dense_diffuse_rounding(torch_cuda, ctx):
+    # At theta = 2 the final N of a dense pair is diffuse: 163 of 400 rows
+    # lose their argmax column to another row, so the rounding is decided by
+    # the augmenting paths.  The permutation must still be the oracle's.
+    g = fi.gaussian_pair(400, jitter=0.01, seed=1)
+    ref = o.fram(g.A, g.B, theta=g.theta)
+    X, P, info = solve_gpu(torch_cuda, ctx, g)
+    check_against_oracle(g, X, P, info, ref)
+    assert info.lap_augmentations >= 100
 
 
 def test_solve_with_node_term(torch_cuda, ctx):
