@@ -42,6 +42,9 @@ WORKLOADS = {
                fi.medium_er_pair),
     "large": ("Gaussian-kernel pair n=8192, sigma=median distance, N(0,0.01) jitter, theta=2",
               fi.large_gaussian_pair),
+    "attributed": ("Gaussian-kernel pair n=1000 with d=128 nonnegative unit node descriptors "
+                   "(N(0,0.5/sqrt(d)) noise on the partner), K = F F~^T computed in the step, "
+                   "theta=2, lambda=1", fi.attributed_medium_pair),
 }
 PRECISIONS = {"fp64": 0, "tf32": 1, "bf16": 2}
 DTYPES = {"fp64": "f64", "tf32": "tf32+f32+f64", "bf16": "bf16+f32+f64"}
@@ -121,12 +124,18 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def oracle_node_term(g):
+    import oracle as o
+    return o.node_affinity(g.F, g.Ft) if g.F is not None else None
+
+
 def oracle_sample(g, outer_full, max_outer):
     """Time the oracle on the first `max_outer` outer iterations of the same
-    solve and scale to one full solve of `outer_full` iterations."""
+    solve (node affinity included) and scale to one full solve of
+    `outer_full` iterations."""
     import oracle as o
     t0 = time.perf_counter()
-    r = o.fram(g.A, g.B, theta=g.theta, max_outer=max_outer)
+    r = o.fram(g.A, g.B, K=oracle_node_term(g), theta=g.theta, max_outer=max_outer)
     dt = time.perf_counter() - t0
     per_iter = dt / r.outer_iters
     return per_iter * outer_full, r.outer_iters, dt
@@ -143,7 +152,7 @@ def run_reference(args):
     # count; each timed step is then a bounded sample of 2 outer iterations,
     # scaled to a full solve.
     t0 = time.perf_counter()
-    full = o.fram(g.A, g.B, theta=g.theta)
+    full = o.fram(g.A, g.B, K=oracle_node_term(g), theta=g.theta)
     t_full = time.perf_counter() - t0
     outer = full.outer_iters
     per = []
@@ -169,14 +178,24 @@ def run_reference(args):
     return 0
 
 
-def time_solves(fr, torch, ctx, n, A, B, params, steps, warmup, flush, count_launches=False):
+def solve_step(fr, ctx, n, A, B, params, X, P, node):
+    """One solve; with node attributes (d, F, Ft, K) the affinity K = F Ft^T
+    is formed first, inside the step."""
+    K = None
+    if node is not None:
+        d, F, Ft, K = node
+        fr.fram_node_affinity(ctx, n, d, F, Ft, K)
+    return fr.fram_solve(ctx, n, A, B, K, params, X, P)
+
+
+def time_solves(fr, torch, ctx, n, A, B, params, steps, warmup, flush, node=None):
     """W untimed solves, then `steps` solves each bracketed by CUDA events on
     the library's stream (L2 flushed before each, outside the events)."""
     X = torch.empty((n, n), dtype=torch.float64, device="cuda")
     P = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        fr.fram_solve(ctx, n, A, B, None, params, X, P)
+        solve_step(fr, ctx, n, A, B, params, X, P, node)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
@@ -185,7 +204,7 @@ def time_solves(fr, torch, ctx, n, A, B, params, steps, warmup, flush, count_lau
     for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
-        _, info = fr.fram_solve(ctx, n, A, B, None, params, X, P)
+        _, info = solve_step(fr, ctx, n, A, B, params, X, P, node)
         ev[k][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
@@ -429,13 +448,18 @@ def run_ours(args):
                                     max_polish=args.polish if mixed else 0)
     A = torch.from_numpy(g.A).to("cuda")
     B = torch.from_numpy(g.B).to("cuda")
+    node = None
+    if g.F is not None:
+        d = g.F.shape[1]
+        node = (d, torch.from_numpy(g.F).to("cuda"), torch.from_numpy(g.Ft).to("cuda"),
+                torch.empty((n, n), dtype=torch.float64, device="cuda"))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if ws > 1:
         torch.distributed.barrier()
 
     with ClockSampler(dev) as clk:
         ms, infos, X, P, launches = time_solves(fr, torch, ctx, n, A, B, params, args.steps,
-                                                args.warmup, flush)
+                                                args.warmup, flush, node)
     total_s = sum(ms) / 1e3
     if ws > 1:
         t = torch.tensor([total_s], device="cuda")
@@ -450,7 +474,7 @@ def run_ours(args):
     if mixed and not args.no_fp64:
         p64 = fr.fram_default_params(theta=g.theta)
         ms64, infos64, X64, P64, _ = time_solves(fr, torch, ctx, n, A, B, p64,
-                                                 max(2, min(args.steps, 5)), 1, flush)
+                                                 max(2, min(args.steps, 5)), 1, flush, node)
         fp64 = {"ms": ms64, "info": infos64[-1], "X": X64.cpu().numpy(), "P": P64.cpu().numpy()}
 
     # End to end through the public API with host buffers: the library copies
@@ -459,18 +483,26 @@ def run_ours(args):
     Bh = torch.from_numpy(g.B).pin_memory()
     Xh = torch.empty((n, n), dtype=torch.float64).pin_memory()
     Ph = torch.empty(n, dtype=torch.int32).pin_memory()
+    node_h2d = 0
+    if node is not None:
+        Fh = torch.from_numpy(g.F).pin_memory()
+        Fth = torch.from_numpy(g.Ft).pin_memory()
+        node_h2d = 2 * g.F.size * 8
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fr.fram_solve(ctx, n, Ah, Bh, None, params, Xh, Ph)
+        if node is not None:   # descriptors host -> device inside the step
+            node[1].copy_(Fh, non_blocking=True)
+            node[2].copy_(Fth, non_blocking=True)
+        solve_step(fr, ctx, n, Ah, Bh, params, Xh, Ph, node)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": ws / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8 + n * 4}
+           "h2d_bytes_per_step": 2 * n * n * 8 + node_h2d, "d2h_bytes_per_step": n * n * 8 + n * 4}
 
     if rank == 0:
         import oracle as o

@@ -226,6 +226,11 @@ def medium_er_pair(seed: int = 0) -> GraphPair:
     return er_pair(1000, 0.05, noise=0.05, flip_frac=0.05, seed=seed, theta=10.0)
 
 
+def attributed_medium_pair(seed: int = 0) -> GraphPair:
+    """n=1000 dense Gaussian-kernel pair with d=128 node descriptors, theta=2."""
+    return attributed_pair(1000, d=128, seed=seed)
+
+
 def large_gaussian_pair(seed: int = 0, n: int = 8192) -> GraphPair:
     """n=8192 dense Gaussian-kernel pair, N(0,0.01) jitter; theta=2."""
     return gaussian_pair(n, jitter=0.01, seed=seed, theta=2.0)
