@@ -62,18 +62,33 @@ __host__ __device__ constexpr size_t batched_smem_bytes(int nt) {
          (size_t)NMAX * sizeof(double) + 64 * sizeof(double);
 }
 
-// Block reductions over NT threads; result broadcast to all threads.
+// Block reductions over NT threads in a fixed order; warp 0 combines the
+// warp results and red[32] broadcasts the total (FP64 instructions are
+// scarce on this GPU, so the second level runs in one warp only).
 template <int NT>
-__device__ __forceinline__ double bsum(double v, double* red) {
-  v = warp_sum(v);
+__device__ __forceinline__ double bsum_level2(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double r = 0.0;
-#pragma unroll
-  for (int w = 0; w < NT / 32; ++w) r += red[w];
-  return r;
+  if (warp == 0) {
+    double r = lane < NT / 32 ? red[lane] : 0.0;
+    r = warp_sum(r);
+    if (lane == 0) red[32] = r;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+template <int NT>
+__device__ __forceinline__ double bsum(double v, double* red) {
+  return bsum_level2<NT>(warp_sum(v), red);
+}
+
+// FP32 warp sums, FP64 across warps.
+template <int NT>
+__device__ __forceinline__ double bsum_f(float v, double* red) {
+  return bsum_level2<NT>((double)warp_sum(v), red);
 }
 
 template <int NT>
@@ -83,10 +98,13 @@ __device__ __forceinline__ double bmax(double v, double* red) {
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double r = -INFINITY;
-#pragma unroll
-  for (int w = 0; w < NT / 32; ++w) r = fmax(r, red[w]);
-  return r;
+  if (warp == 0) {
+    double r = lane < NT / 32 ? red[lane] : -INFINITY;
+    r = warp_max(r);
+    if (lane == 0) red[32] = r;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 __device__ __forceinline__ double relu_d(double y) {
@@ -134,13 +152,26 @@ __device__ __forceinline__ T small_gemm(const T* __restrict__ Aop, const T* __re
   return mx;
 }
 
+// Per-sweep scalars, formed once by thread 0 (FP64 instructions are scarce
+// on this GPU, so no other thread touches them): S = sum Y, gamma = S/n - 1,
+// the stop flag gamma <= gamma_tol, and c1 = 1/n + S/n^2 in the working type.
+template <typename T>
+struct SweepCtl {
+  double S, g;
+  double delta, prev_delta;  // outer-iteration test state (thread 0)
+  double inv_sq, inv_n;      // per-pair scalars
+  T c1;
+  int conv, stop;
+};
+
 // One pass of SDSN on Ys (n x n): FIRST scales by `scale`; otherwise the fused
 // P1+P2 sweep with arow/bcol.  Leaves row sums in rs, column sums in cs and
-// returns S (FP64) to every thread.
+// the sweep scalars in *ctl, visible to every thread on return.
 template <typename T, int NT, bool FIRST>
-__device__ __forceinline__ double small_sdsn_pass(T* Ys, T* rs, T* cs, const T* arow,
-                                                  const T* bcol, T* cpart, double* red, int n,
-                                                  T scale) {
+__device__ __forceinline__ void small_sdsn_pass(T* Ys, T* rs, T* cs, const T* arow,
+                                                const T* bcol, T* cpart, SweepCtl<T>* ctl, int n,
+                                                T scale, double inv_n, double inv_n2,
+                                                double gtol) {
   constexpr int G = NT / 64;  // row groups
   const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
   if (c < n) {
@@ -176,10 +207,15 @@ __device__ __forceinline__ double small_sdsn_pass(T* Ys, T* rs, T* cs, const T* 
     if (tid < n) s += (double)rs[tid];
     if (tid + 32 < n) s += (double)rs[tid + 32];
     s = warp_sum(s);
-    if (tid == 0) red[32] = s;
+    if (tid == 0) {
+      const double g = s * inv_n - 1.0;
+      ctl->S = s;
+      ctl->g = g;
+      ctl->conv = g <= gtol;
+      ctl->c1 = (T)(inv_n + s * inv_n2);
+    }
   }
   __syncthreads();
-  return red[32];
 }
 
 // Warp 0: Hungarian on W (n x n, row stride NMAX) for maximum sum.  Lane l
@@ -303,6 +339,7 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
   double* u = reinterpret_cast<double*>(cpart + (NT / 64) * NMAX);
   double* red = u + NMAX;  // [0,32) reductions, [32] broadcast slot
   __shared__ int s_pair, s_aug;
+  __shared__ SweepCtl<T> ctl;
   __shared__ int rowcol[NMAX], argc[NMAX];
   __shared__ double rowmax[NMAX];
   const int tid = threadIdx.x, c = tid & 63, rg = tid >> 6;
@@ -320,24 +357,38 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
     const double* Bg = a.B + d.off_mat;
     BatchInfo info{};
 
-    // Validation (Sec. 3 graph model, reading (vii)) and max for the prescale.
-    double mA = 0.0, mB = 0.0, asA = 0.0, asB = 0.0, bad = 0.0;
+    // Validation (Sec. 3 graph model, reading (vii)) and max for the prescale,
+    // on bit patterns: a finite value >= 0 has sign 0 and exponent < 0x7ff,
+    // and such values order like their bits.  Only entries that differ from
+    // their transpose pay for an FP64 subtraction.
+    unsigned long long mAb = 0, mBb = 0;
+    double asA = 0.0, asB = 0.0;
+    int badi = 0;
     for (int e = tid; e < n * n; e += NT) {
       const int i = e / n, j = e - i * n;
-      const double x = Ag[e], y = Bg[e];
-      if (!isfinite(x) || x < 0.0 || !isfinite(y) || y < 0.0) {
-        bad = 1.0;
+      const unsigned long long xb = (unsigned long long)__double_as_longlong(Ag[e]);
+      const unsigned long long yb = (unsigned long long)__double_as_longlong(Bg[e]);
+      // valid: finite and >= 0, i.e. +0..+max finite, or -0
+      const bool okx = xb < 0x7ff0000000000000ull || xb == 0x8000000000000000ull;
+      const bool oky = yb < 0x7ff0000000000000ull || yb == 0x8000000000000000ull;
+      if (!okx || !oky) {
+        badi = 1;
         continue;
       }
-      mA = fmax(mA, x);
-      mB = fmax(mB, y);
-      const double xt = Ag[j * n + i], yt = Bg[j * n + i];
-      if (isfinite(xt)) asA = fmax(asA, fabs(x - xt));
-      if (isfinite(yt)) asB = fmax(asB, fabs(y - yt));
+      mAb = mAb > (xb & 0x7fffffffffffffffull) ? mAb : (xb & 0x7fffffffffffffffull);
+      mBb = mBb > (yb & 0x7fffffffffffffffull) ? mBb : (yb & 0x7fffffffffffffffull);
+      const unsigned long long xtb = (unsigned long long)__double_as_longlong(Ag[j * n + i]);
+      const unsigned long long ytb = (unsigned long long)__double_as_longlong(Bg[j * n + i]);
+      if (xtb != xb && xtb < 0x7ff0000000000000ull)
+        asA = fmax(asA, fabs(__longlong_as_double((long long)xb) -
+                             __longlong_as_double((long long)xtb)));
+      if (ytb != yb && ytb < 0x7ff0000000000000ull)
+        asB = fmax(asB, fabs(__longlong_as_double((long long)yb) -
+                             __longlong_as_double((long long)ytb)));
     }
-    bad = bmax<NT>(bad, red);
-    mA = bmax<NT>(mA, red);
-    mB = bmax<NT>(mB, red);
+    const double bad = bmax<NT>(badi ? 1.0 : 0.0, red);
+    const double mA = bmax<NT>(__longlong_as_double((long long)mAb), red);
+    const double mB = bmax<NT>(__longlong_as_double((long long)mBb), red);
     asA = bmax<NT>(asA, red);
     asB = bmax<NT>(asB, red);
     const double cc = fmax(mA, mB);
@@ -351,22 +402,28 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       continue;
     }
     // Alg. 1 steps 2-3 and the initial N (reading (i)), zero-padded tiles.
-    const double sq = sqrt(cc);
-    const double n0 = 1.0 / n;
+    // Scalars once, in thread 0: 1/sqrt(c) scales both graphs by one multiply.
+    if (tid == 0) {
+      ctl.inv_sq = 1.0 / sqrt(cc);
+      ctl.inv_n = 1.0 / n;
+    }
+    __syncthreads();
+    const double inv_n = ctl.inv_n, n0 = inv_n;
+    const T inv_n_t = (T)inv_n, inv_sq_t = (T)ctl.inv_sq;
     for (int e = tid; e < NMAX * NMAX; e += NT) {
       const int i = e >> 6, j = e & 63;
       const bool in = i < n && j < n;
-      As[i * LDS + j] = in ? (T)(Ag[i * n + j] / sq) : T(0);
-      Bs[i * LDS + j] = in ? (T)(Bg[i * n + j] / sq) : T(0);
-      Nc[i * LDS + j] = in ? (T)n0 : T(0);
-      N64[i * NMAX + j] = in ? n0 : 0.0;
+      As[i * LDS + j] = in ? (T)Ag[i * n + j] * inv_sq_t : T(0);
+      Bs[i * LDS + j] = in ? (T)Bg[i * n + j] * inv_sq_t : T(0);
+      Nc[i * LDS + j] = in ? inv_n_t : T(0);
+      if (sizeof(T) == 8) N64[i * NMAX + j] = in ? n0 : 0.0;
     }
     __syncthreads();
 
-    const double inv_n = 1.0 / n, inv_n2 = inv_n * inv_n;
-    const T inv_n_t = (T)inv_n;
+    const double inv_n2 = inv_n * inv_n;
     const double gtol = a.gamma_tol;
-    double prev_delta = INFINITY, delta = INFINITY, g = INFINITY;
+    double delta = INFINITY, g = INFINITY;
+    if (tid == 0) ctl.prev_delta = INFINITY;
     int t = 0, sweeps_total = 0;
     while (t < a.max_outer) {
       // Step 5: T = A N, X = T B.
@@ -374,57 +431,95 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       __syncthreads();
       const T lm = small_gemm<T, NT>(Ts, Bs, Ys, n, true);
       const double m = bmax<NT>((double)lm, red);
-      if (!(m > 0.0)) {
+      if (tid == 0) {
+        ctl.conv = !(m > 0.0);  // degenerate: max X <= 0
+        ctl.c1 = (T)((a.theta / 2.0) / m);
+      }
+      __syncthreads();
+      if (ctl.conv) {
         info.status = PAIR_DEGENERATE;
         break;
       }
       // Step 6: SDSN.
-      double S = small_sdsn_pass<T, NT, true>(Ys, rs, cs, arow, bcol, cpart, red, n,
-                                              (T)((a.theta / 2.0) / m));
+      small_sdsn_pass<T, NT, true>(Ys, rs, cs, arow, bcol, cpart, &ctl, n, ctl.c1, inv_n, inv_n2,
+                                   gtol);
       int k = 0;
       while (true) {
-        if (k > 0) {
-          g = S * inv_n - 1.0;
-          if (g <= gtol) break;
-        }
+        if (k > 0 && ctl.conv) break;  // gamma of the last clamped result (reading (iii))
         if (k >= a.max_sweeps) break;
-        const T c1 = (T)(inv_n + S * inv_n2);
+        const T c1 = ctl.c1;
         if (tid < n) {
           arow[tid] = c1 - rs[tid] * inv_n_t;
           bcol[tid] = cs[tid] * inv_n_t;
         }
         __syncthreads();
-        S = small_sdsn_pass<T, NT, false>(Ys, rs, cs, arow, bcol, cpart, red, n, T(1));
+        small_sdsn_pass<T, NT, false>(Ys, rs, cs, arow, bcol, cpart, &ctl, n, T(1), inv_n, inv_n2,
+                                      gtol);
         ++k;
       }
+      if (k > 0) g = ctl.g;
       sweeps_total += k;
-      // Steps 7-8 in FP64.
+      // Steps 7-8.  FP64 path: N in FP64.  FP32 path: N in FP32 with each
+      // thread's few squared terms summed in FP32 and the block sums and the
+      // delta test in FP64.
       double d2 = 0.0, nn2 = 0.0;
-      if (c < n)
-        for (int r = rg; r < n; r += G) {
-          const double old = N64[r * NMAX + c];
-          const double nn = __dadd_rn(__dmul_rn(1.0 - a.alpha, old),
-                                      __dmul_rn(a.alpha, (double)Ys[r * LDS + c]));
-          const double dd = __dsub_rn(nn, old);
-          N64[r * NMAX + c] = nn;
-          Nc[r * LDS + c] = (T)nn;
-          d2 = fma(dd, dd, d2);
-          nn2 = fma(nn, nn, nn2);
+      float d2f = 0.0f, nn2f = 0.0f;
+      if (c < n) {
+        if (sizeof(T) == 8) {
+          for (int r = rg; r < n; r += G) {
+            const double old = N64[r * NMAX + c];
+            const double nn = __dadd_rn(__dmul_rn(1.0 - a.alpha, old),
+                                        __dmul_rn(a.alpha, (double)Ys[r * LDS + c]));
+            const double dd = __dsub_rn(nn, old);
+            N64[r * NMAX + c] = nn;
+            Nc[r * LDS + c] = (T)nn;
+            d2 = fma(dd, dd, d2);
+            nn2 = fma(nn, nn, nn2);
+          }
+        } else {
+          const float al = (float)a.alpha, bl = (float)(1.0 - a.alpha);
+          for (int r = rg; r < n; r += G) {
+            const float old = (float)Nc[r * LDS + c];
+            const float nn = fmaf(bl, old, al * (float)Ys[r * LDS + c]);
+            const float dd = nn - old;
+            Nc[r * LDS + c] = (T)nn;
+            d2f = fmaf(dd, dd, d2f);
+            nn2f = fmaf(nn, nn, nn2f);
+          }
         }
-      d2 = bsum<NT>(d2, red);
-      nn2 = bsum<NT>(nn2, red);
-      delta = sqrt(d2) / sqrt(nn2);
+      }
+      if (sizeof(T) == 8) {
+        d2 = bsum<NT>(d2, red);
+        nn2 = bsum<NT>(nn2, red);
+      } else {
+        d2 = bsum_f<NT>(d2f, red);
+        nn2 = bsum_f<NT>(nn2f, red);
+      }
       ++t;
-      if (delta <= a.delta_tol || (a.use_stall && delta <= a.mixed_delta_tol)) break;
-      if (a.use_stall && a.stall_ratio > 0.0 && delta <= a.stall_below &&
-          delta > a.stall_ratio * prev_delta)
-        break;
-      prev_delta = delta;
+      // Alg. 1 steps 7-8 test (and the mixed stop rules), thread 0 only.
+      if (tid == 0) {
+        const double dl = sqrt(d2) / sqrt(nn2);
+        int stop = dl <= a.delta_tol || (a.use_stall && dl <= a.mixed_delta_tol);
+        if (a.use_stall && a.stall_ratio > 0.0 && dl <= a.stall_below &&
+            dl > a.stall_ratio * ctl.prev_delta)
+          stop = 1;
+        ctl.prev_delta = dl;
+        ctl.delta = dl;
+        ctl.stop = stop;
+      }
+      __syncthreads();
+      delta = ctl.delta;
+      if (ctl.stop) break;
     }
     __syncthreads();
     if (info.status != PAIR_OK) {
       if (tid == 0) a.info[pi] = info;
       continue;
+    }
+    if (sizeof(T) == 4) {  // the rounding and the output read N in FP64
+      for (int e = tid; e < NMAX * NMAX; e += NT)
+        N64[e] = (double)Nc[(e >> 6) * LDS + (e & 63)];
+      __syncthreads();
     }
     // Step 10 (eq. 2): warp 0.
     if (tid < 32) small_lap(N64, n, u, rowcol, argc, rowmax, &s_aug);

@@ -8,17 +8,21 @@
 // Inputs are BF16 (tcgen05.mma kind::f16) or TF32-rounded FP32 (kind::tf32);
 // accumulation is FP32 in tensor memory.
 //
-// One CTA computes one 128 x 128 output tile:
+// Persistent, warp-specialised: one CTA per SM walks its share of the
+// 128 x BN output tiles (BN = 256 for large ld, else 128) in a grouped order
+// (8 row panels at a time, so concurrent CTAs share A and B strips in L2):
 //   warp 0     TMA producer: 128-byte-swizzled A/B k-slices into a 4-stage
 //              shared-memory ring (mbarrier full/empty pairs)
-//   warp 1     allocates 128 TMEM columns; one elected thread issues the
-//              tcgen05.mma instructions (M=128, N=128, K=16 or 8 each) and
-//              commits each stage back to its empty barrier
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (each warp reads its
-//              own 32-lane quarter of TMEM), optional + lambda K, max(C), and
-//              the store in the output precision
+//   warp 1     allocates 2 x BN TMEM columns (two accumulators); one elected
+//              thread issues the tcgen05.mma instructions (M=128, N=BN, K=16
+//              or 8 each), commits each stage back to its empty barrier and
+//              each finished tile to its accumulator's full barrier
+//   warps 2-5  epilogue: tcgen05.ld of an accumulator (each warp reads its
+//              own 32-lane quarter of TMEM), optional + lambda K, max(C), the
+//              store in the output precision, then the accumulator is handed
+//              back; the next tile's MMAs meanwhile fill the other one
 // Every mbarrier wait is limited in time; on expiry the kernel records an
-// error, drains its own TMA copies, frees TMEM and returns.
+// error, drains its own TMA copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -31,13 +35,20 @@ namespace fram {
 
 namespace {
 
-constexpr int BM = 128, BN = 128;
+constexpr int BM = 128;
 constexpr int ROW_BYTES = 128;              // one swizzle atom row per k-slice
 constexpr int STAGES = 4;
-constexpr int TILE_BYTES = BM * ROW_BYTES;  // 16 KiB per operand per stage
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
+constexpr int A_BYTES = BM * ROW_BYTES;     // 16 KiB of A per stage
 constexpr int GEMM_THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int GROUP_M = 8;                  // row panels per rasterisation group
+
+template <int BN>
+struct Cfg {
+  static constexpr int B_BYTES = BN * ROW_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = 2 * BN;  // two accumulators
+};
 
 struct GemmArgs {
   int ld;                  // M = N = K = ld (multiple of 128)
@@ -110,9 +121,9 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 // Instruction descriptor: FP32 accumulator (bits [4,6) = 1), A/B format in
 // [7,10)/[10,13) (BF16 = 1, TF32 = 2), both K-major, N >> 3 in [17,23),
 // M >> 4 in [24,29).
-__host__ __device__ constexpr uint32_t instr_desc(int kind) {
+__host__ __device__ constexpr uint32_t instr_desc(int kind, int bn) {
   return (1u << 4) | ((kind == 0 ? 1u : 2u) << 7) | ((kind == 0 ? 1u : 2u) << 10) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <int KIND>
@@ -166,41 +177,57 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-template <int KIND>
+// Tile t of the grouped order -> (row panel, column panel).
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int per_group = GROUP_M * tiles_n;
+  const int g = t / per_group, r = t % per_group;
+  const int first = g * GROUP_M;
+  const int gm = min(GROUP_M, tiles_m - first);
+  tm = first + r % gm;
+  tn = r / gm;
+}
+
+template <int KIND, int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    GemmArgs g) {
+  using C = Cfg<BN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ float s_max[4];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024 - (raw & 1023)) & 1023);
   const uint32_t sbase = smem_u32(smem);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES, done = empty0 + 8 * STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
+  // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES;
+  const uint32_t accf0 = empty0 + 8 * STAGES, acce0 = accf0 + 16, drain = acce0 + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* s_consumed = s_fail + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   constexpr int KELEMS = KIND == 0 ? 64 : 32;     // elements per 128-byte row
   constexpr int UMMA_K_BYTES = 32;                 // K=16 BF16 or K=8 TF32 per MMA
   const int nkb = g.ld / KELEMS;
+  const int tiles_m = g.ld / BM, tiles_n = (g.ld + BN - 1) / BN;
+  const int ntiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
     *s_fail = 0;
-    *s_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -211,83 +238,108 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1, g.limit_ns)) {
-          *s_fail = 1;
-          break;
+      long long issued = 0, it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*s_fail; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, tm, tn);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+          if (it >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1, g.limit_ns)) {
+            *s_fail = 1;
+            break;
+          }
+          if (*s_fail) break;
+          const uint32_t fb = full0 + 8 * s;
+          mbar_expect_tx(fb, C::STAGE_BYTES);
+          tma_load_2d(sbase + s * C::STAGE_BYTES, &tmA, kb * KELEMS, tm * BM, fb);
+          tma_load_2d(sbase + s * C::STAGE_BYTES + A_BYTES, &tmB, kb * KELEMS, tn * BN, fb);
+          issued = it + 1;
         }
-        if (*s_fail) break;
-        const uint32_t fb = full0 + 8 * s;
-        mbar_expect_tx(fb, STAGE_BYTES);
-        tma_load_2d(sbase + s * STAGE_BYTES, &tmA, kb * KELEMS, m0, fb);
-        tma_load_2d(sbase + s * STAGE_BYTES + TILE_BYTES, &tmB, kb * KELEMS, n0, fb);
-        issued = kb + 1;
       }
       if (*s_fail) {
-        // Drain: wait (limited) for our own copies that nobody consumed.
-        const int consumed = *s_consumed;
-        for (int kb = consumed; kb < issued; ++kb)
-          mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, g.limit_ns);
+        // Drain: wait (limited) for our own copies; the last STAGES issued
+        // may still be in flight whether or not they were consumed.
+        for (long long k = issued > STAGES ? issued - STAGES : 0; k < issued; ++k)
+          mbar_wait(full0 + 8 * (int)(k % STAGES), (uint32_t)((k / STAGES) & 1), g.limit_ns);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(KIND);
+      const uint32_t idesc = instr_desc(KIND, BN);
+      long long it = 0;
+      int i = 0;
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, g.limit_ns) || *s_fail) {
-          *s_fail = 1;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+        if (i >= 2 && !mbar_wait(acce0 + 8 * buf, ((i >> 1) & 1) ^ 1, g.limit_ns)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t a_addr = sbase + s * STAGE_BYTES;
-        const uint32_t b_addr = a_addr + TILE_BYTES;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % STAGES);
+          if (!mbar_wait(full0 + 8 * s, (uint32_t)((it / STAGES) & 1), g.limit_ns) || *s_fail) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = sbase + s * C::STAGE_BYTES;
+          const uint32_t b_addr = a_addr + A_BYTES;
 #pragma unroll
-        for (int k = 0; k < ROW_BYTES / UMMA_K_BYTES; ++k) {
-          mma<KIND>(tmem, smem_desc_sw128(a_addr + k * UMMA_K_BYTES),
-                    smem_desc_sw128(b_addr + k * UMMA_K_BYTES), idesc, (kb | k) != 0 ? 1u : 0u);
+          for (int k = 0; k < ROW_BYTES / UMMA_K_BYTES; ++k) {
+            mma<KIND>(acc, smem_desc_sw128(a_addr + k * UMMA_K_BYTES),
+                      smem_desc_sw128(b_addr + k * UMMA_K_BYTES), idesc, (kb | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(empty0 + 8 * s);
         }
-        mma_commit(empty0 + 8 * s);
-        *s_consumed = kb + 1;
+        if (!ok) break;
+        mma_commit(accf0 + 8 * buf);
       }
-      // Signal the epilogue; on failure this still tracks the MMAs issued so
-      // far, so TMEM is only released after they finish.
-      mma_commit(done);
-      if (!ok) mbar_wait(done, 0, g.limit_ns);
+      if (!ok) {
+        *s_fail = 1;
+        // Let every MMA issued so far finish before TMEM is released.
+        mma_commit(drain);
+        mbar_wait(drain, 0, g.limit_ns);
+      }
     }
   } else {
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = m0 + q * 32 + lane;
     float lmax = -INFINITY;
-    const bool ready = mbar_wait(done, 0, g.limit_ns) && !*s_fail;
-    if (!ready) *s_fail = 1;
-    if (ready) {
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      if (!mbar_wait(accf0 + 8 * buf, (uint32_t)((i >> 1) & 1), g.limit_ns) || *s_fail) {
+        *s_fail = 1;
+        break;
+      }
       tc_fence_after();
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, tm, tn);
+      const int row = tm * BM + q * 32 + lane;
+      const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
-        const int col0 = n0 + c0;
+        tmem_ld16(acc + c0, v);
+        const int col0 = tn * BN + c0;
+        if (col0 >= g.ld) break;  // past the last column (partial BN tile)
         if (g.Kmat != nullptr && row < g.n) {
           const double* kr = g.Kmat + (size_t)row * g.ld + col0;
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (col0 + i < g.n) v[i] += (float)(g.lam * kr[i]);
+          for (int e = 0; e < 16; ++e)
+            if (col0 + e < g.n) v[e] += (float)(g.lam * kr[e]);
         }
         if (g.cmax != nullptr && row < g.n) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (col0 + i < g.n) lmax = fmaxf(lmax, v[i]);
+          for (int e = 0; e < 16; ++e)
+            if (col0 + e < g.n) lmax = fmaxf(lmax, v[e]);
         }
         if (g.out_kind == 1) {
           __nv_bfloat162 h[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
           uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(g.C) +
                                                 (size_t)row * g.ld + col0);
           dst[0] = *reinterpret_cast<uint4*>(&h[0]);
@@ -295,15 +347,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         } else {
           if (g.out_kind == 2) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = to_tf32(v[i]);
+            for (int e = 0; e < 16; ++e) v[e] = to_tf32(v[e]);
           }
           float4* dst = reinterpret_cast<float4*>(static_cast<float*>(g.C) + (size_t)row * g.ld +
                                                   col0);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2],
-                                                           v[4 * i + 3]);
+          for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2],
+                                                           v[4 * e + 3]);
         }
       }
+      // Hand the accumulator back to the MMA warp.
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * buf)
+                                  : "memory");
     }
     if (g.cmax != nullptr) {
 #pragma unroll
@@ -315,7 +372,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
                  : "memory");
   }
   if (threadIdx.x == 0) {
@@ -340,19 +398,50 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* ptr, int ld, int kind) {
+bool make_map(CUtensorMap* m, const void* ptr, int ld, int kind, int box_rows) {
   auto enc = get_encode();
   if (!enc) return false;
   const size_t es = kind == 0 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ld};
   cuuint64_t strides[1] = {(cuuint64_t)ld * es};
-  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es), (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                    2, const_cast<void*>(ptr), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+namespace {
+
+int num_sms_cached() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+      v = 1;
+  }
+  return v;
+}
+
+template <int KIND, int BN>
+int launch_k(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, int ld,
+             cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(gemm_tc_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<BN>::SMEM_BYTES) != cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  const int ntiles = (ld / BM) * ((ld + BN - 1) / BN);
+  const int grid = ntiles < num_sms_cached() ? ntiles : num_sms_cached();
+  gemm_tc_kernel<KIND, BN><<<grid, GEMM_THREADS, Cfg<BN>::SMEM_BYTES, s>>>(ma, mb, g);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace
@@ -364,8 +453,11 @@ int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int k
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bop) |
        reinterpret_cast<uintptr_t>(C)) & 15)
     return -1;
+  // 256-wide tiles once every CTA gets at least two of them.
+  const bool wide = (ld / BM) * ((ld + 255) / 256) >= 2 * num_sms_cached();
+  const int bn = wide ? 256 : 128;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, ld, kind) || !make_map(&mb, Bop, ld, kind)) return -1;
+  if (!make_map(&ma, A, ld, kind, BM) || !make_map(&mb, Bop, ld, kind, bn)) return -1;
   GemmArgs g{};
   g.ld = ld;
   g.n = n;
@@ -377,27 +469,8 @@ int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int k
   g.cmax = cmax;
   g.err = err;
   g.limit_ns = limit_ns;
-  dim3 grid(ld / BN, ld / BM);
-  if (kind == 0) {
-    static bool attr0 = false;
-    if (!attr0) {
-      if (cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               SMEM_BYTES) != cudaSuccess)
-        return -1;
-      attr0 = true;
-    }
-    gemm_tc_kernel<0><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
-  } else {
-    static bool attr1 = false;
-    if (!attr1) {
-      if (cudaFuncSetAttribute(gemm_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               SMEM_BYTES) != cudaSuccess)
-        return -1;
-      attr1 = true;
-    }
-    gemm_tc_kernel<1><<<grid, GEMM_THREADS, SMEM_BYTES, s>>>(ma, mb, g);
-  }
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+  if (kind == 0) return wide ? launch_k<0, 256>(ma, mb, g, ld, s) : launch_k<0, 128>(ma, mb, g, ld, s);
+  return wide ? launch_k<1, 256>(ma, mb, g, ld, s) : launch_k<1, 128>(ma, mb, g, ld, s);
 }
 
 }  // namespace fram
