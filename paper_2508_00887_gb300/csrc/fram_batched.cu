@@ -55,9 +55,13 @@ struct BatchArgs {
 
 enum : int { PAIR_OK = 0, PAIR_INVALID = 1, PAIR_DEGENERATE = 2 };
 
+// Shared memory of one CTA: five tiles (A, B, N, T, X/Y), the FP64 copy of
+// N (FP64 path only: the FP32 path keeps N in FP32 and fits two CTAs per
+// SM), the SDSN vectors and partials, the row potentials and reductions.
 template <typename T>
 __host__ __device__ constexpr size_t batched_smem_bytes(int nt) {
-  return 5 * (size_t)NMAX * LDS * sizeof(T) + (size_t)NMAX * NMAX * sizeof(double) +
+  return 5 * (size_t)NMAX * LDS * sizeof(T) +
+         (sizeof(T) == 8 ? (size_t)NMAX * NMAX * sizeof(double) : 0) +
          4 * (size_t)NMAX * sizeof(T) + (size_t)(nt / 64) * NMAX * sizeof(T) +
          (size_t)NMAX * sizeof(double) + 64 * sizeof(double);
 }
@@ -220,7 +224,8 @@ __device__ __forceinline__ void small_sdsn_pass(T* Ys, T* rs, T* cs, const T* ar
 
 // Warp 0: Hungarian on W (n x n, row stride NMAX) for maximum sum.  Lane l
 // owns columns l and l + 32; row potentials live in shared memory.
-__device__ void small_lap(const double* W, int n, double* u, int* rowcol, int* argc,
+template <typename TW>
+__device__ void small_lap(const TW* W, int ldw, int n, double* u, int* rowcol, int* argc,
                           double* rowmax, int* aug_out) {
   const int lane = threadIdx.x & 31;
   // Row argmax (ties -> lowest column).
@@ -228,7 +233,7 @@ __device__ void small_lap(const double* W, int n, double* u, int* rowcol, int* a
     double best = -INFINITY;
     int bj = 0x7fffffff;
     for (int j = lane; j < n; j += 32) {
-      const double x = W[i * NMAX + j];
+      const double x = (double)W[i * ldw + j];
       if (x > best) { best = x; bj = j; }
     }
 #pragma unroll
@@ -273,7 +278,7 @@ __device__ void small_lap(const double* W, int n, double* u, int* rowcol, int* a
       for (int s = 0; s < 2; ++s) {
         const int j = lane + 32 * s;
         if (j < n && !used[s]) {
-          const double cur = -W[i0 * NMAX + j] - ui - v[s];
+          const double cur = -(double)W[i0 * ldw + j] - ui - v[s];
           if (cur < minv[s]) { minv[s] = cur; way[s] = j0; }
           if (minv[s] < best) { best = minv[s]; bj = j; }
         }
@@ -323,15 +328,15 @@ __device__ void small_lap(const double* W, int n, double* u, int* rowcol, int* a
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) batched_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* As = reinterpret_cast<T*>(smem);
   T* Bs = As + NMAX * LDS;
   T* Nc = Bs + NMAX * LDS;
   T* Ts = Nc + NMAX * LDS;
   T* Ys = Ts + NMAX * LDS;
-  double* N64 = reinterpret_cast<double*>(Ys + NMAX * LDS);
-  T* rs = reinterpret_cast<T*>(N64 + NMAX * NMAX);
+  double* N64 = reinterpret_cast<double*>(Ys + NMAX * LDS);  // FP64 path only
+  T* rs = reinterpret_cast<T*>(N64 + (sizeof(T) == 8 ? NMAX * NMAX : 0));
   T* cs = rs + NMAX;
   T* arow = cs + NMAX;
   T* bcol = arow + NMAX;
@@ -516,13 +521,13 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       if (tid == 0) a.info[pi] = info;
       continue;
     }
-    if (sizeof(T) == 4) {  // the rounding and the output read N in FP64
-      for (int e = tid; e < NMAX * NMAX; e += NT)
-        N64[e] = (double)Nc[(e >> 6) * LDS + (e & 63)];
-      __syncthreads();
+    // Step 10 (eq. 2): warp 0, on N as kept (FP64 path: FP64 copy).
+    if (tid < 32) {
+      if (sizeof(T) == 8)
+        small_lap(N64, NMAX, n, u, rowcol, argc, rowmax, &s_aug);
+      else
+        small_lap(Nc, LDS, n, u, rowcol, argc, rowmax, &s_aug);
     }
-    // Step 10 (eq. 2): warp 0.
-    if (tid < 32) small_lap(N64, n, u, rowcol, argc, rowmax, &s_aug);
     __syncthreads();
     // Objective (eq. 1) and matching error (Sec. 7) on the unscaled inputs.
     double s1 = 0.0, s2 = 0.0;
@@ -534,7 +539,8 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       s2 = fma(x - y, x - y, s2);
     }
     double av = 0.0;
-    if (tid < n) av = N64[tid * NMAX + rowcol[tid]];
+    if (tid < n)
+      av = sizeof(T) == 8 ? N64[tid * NMAX + rowcol[tid]] : (double)Nc[tid * LDS + rowcol[tid]];
     s1 = bsum<NT>(s1, red);
     s2 = bsum<NT>(s2, red);
     av = bsum<NT>(av, red);
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(BatchArgs a) {
       double* no = a.Nout + d.off_mat;
       for (int e = tid; e < n * n; e += NT) {
         const int i = e / n, j = e - i * n;
-        no[e] = N64[i * NMAX + j];
+        no[e] = sizeof(T) == 8 ? N64[i * NMAX + j] : (double)Nc[i * LDS + j];
       }
     }
     if (tid == 0) {
@@ -624,10 +630,30 @@ void set_attrs() {
   done = true;
 }
 
+// Resident CTAs per SM for a block size (queried once).
+template <typename T>
+int batched_occupancy(int nt) {
+  static int occ[3] = {0, 0, 0};
+  const int k = nt == 128 ? 0 : (nt == 256 ? 1 : 2);
+  if (occ[k] == 0) {
+    int v = 0;
+    cudaError_t e =
+        nt == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_kernel<T, 128>, 128,
+                                                                  batched_smem_bytes<T>(128))
+        : nt == 256 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_kernel<T, 256>, 256,
+                                                                    batched_smem_bytes<T>(256))
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_kernel<T, 512>, 512,
+                                                                    batched_smem_bytes<T>(512));
+    occ[k] = (e == cudaSuccess && v > 0) ? v : 1;
+  }
+  return occ[k];
+}
+
 template <typename T>
 int launch_batched(const BatchArgs& a, int nt, int num_sms, cudaStream_t s) {
   set_attrs<T>();
-  int grid = num_sms < a.count ? num_sms : a.count;
+  const int slots = batched_occupancy<T>(nt) * num_sms;
+  int grid = slots < a.count ? slots : a.count;
   if (grid < 1) grid = 1;
   switch (nt) {
     case 128:
@@ -814,7 +840,7 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
   if (nt == 0) {
     float best = 1e30f;
     BatchArgs t = a;
-    t.count = std::min(count, 2 * c->num_sms);
+    t.count = std::min(count, 4 * c->num_sms);
     for (int cand : {128, 256, 512}) {
       BT_CUDA(cudaMemsetAsync(S.queue, 0, 4, s), "memset");
       BT_CUDA(cudaEventRecord(c->ev0, s), "event");

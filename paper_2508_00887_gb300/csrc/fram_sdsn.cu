@@ -288,8 +288,9 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
 template <typename T, typename TIn, int MAXC>
 __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int nblk,
                                           unsigned char* smem) {
-  __shared__ int s_flag;
-  __shared__ double s_S;
+  __shared__ int s_flag, s_stop;
+  __shared__ double s_g;
+  __shared__ T s_cS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bi = blk / p.Q, bj = blk % p.Q;
   const int r0 = bi * p.tr, c0 = bj * p.tc;
@@ -345,12 +346,19 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
   int k = 0;
   while (true) {
     const int rb = k & 1;
-    // One round trip: totals (warp 0), row partials, column partials.
+    // One round trip: totals (warp 0), row partials, column partials.  The
+    // scalars S, gamma, the stop test and S/n^2 are formed once, by lane 0 of
+    // warp 0 (FP64 instructions are scarce on this GPU).
     if (warp == 0) {
       double s = 0.0;
       for (unsigned t = lane; t < nblocks; t += 32) s += __ldcg(&p.tpart[(size_t)rb * nblocks + t]);
       s = warp_sum(s);
-      if (lane == 0) s_S = s;
+      if (lane == 0) {
+        const double gk = s * inv_n - 1.0;
+        s_g = gk;
+        s_stop = (k > 0 || p.mode == 1) && gk <= p.gamma_tol;
+        s_cS = (T)(s * inv_n2);
+      }
     }
     for (int e = tid; e < nr + nc; e += kSdsnThreads) {
       const bool is_row = e < nr;
@@ -372,14 +380,11 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
         bcol[idx] = acc * inv_n_t;
     }
     __syncthreads();
-    const double S = s_S;
-    if (k > 0 || p.mode == 1) {
-      g = S * inv_n - 1.0;
-      if (g <= p.gamma_tol) break;
-    }
+    if (k > 0 || p.mode == 1) g = s_g;
+    if (s_stop) break;
     if (k >= max_sweeps) break;
     sdsn_pass<T, TIn, MAXC, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi,
-                                   bj, scale, rb ^ 1, blk, nblk, (T)(S * inv_n2));
+                                   bj, scale, rb ^ 1, blk, nblk, s_cS);
     ++k;
     ++epoch;
     if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
