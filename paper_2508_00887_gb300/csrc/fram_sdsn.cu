@@ -89,7 +89,7 @@ __device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
+    // The barrier above orders the CTA's writes before thread 0's release.
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
     if ((int)(ld_acquire_u32(&b->count) - target) < 0) {
       const uint64_t t0 = globaltimer_ns();
@@ -269,18 +269,34 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
   __syncthreads();
   T* rp = p.rpart + ((size_t)wb * p.Q + bj) * p.n + r0;
   for (int i = tid; i < nr; i += kSdsnThreads) rp[i] = rowsum[i];
+  // Column sums: four threads per column add four warps' values each, then
+  // combine with two shuffles (a fixed order).
   T* cp = p.cpart + ((size_t)wb * p.P + bi) * p.n + c0;
-  for (int j = tid; j < nc; j += kSdsnThreads) {
+  for (int base = 0; base < nc; base += kSdsnThreads / 4) {
+    const int j = base + (tid >> 2), part = tid & 3;
     T c = T(0);
+    if (j < nc) {
 #pragma unroll
-    for (int w = 0; w < kSdsnWarps; ++w) c += colacc[w * p.tc + j];
-    cp[j] = c;
+      for (int w = part; w < kSdsnWarps; w += 4) c += colacc[w * p.tc + j];
+    }
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    if (part == 0 && j < nc) cp[j] = c;
   }
   if (warp == 0) {
-    double t = 0.0;
-    for (int i = lane; i < nr; i += 32) t += (double)rowsum[i];
-    t = warp_sum(t);
-    if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = t;
+    // Tile total for S: FP64 in the FP64 kernel; from the FP32 row sums in
+    // one FP32 warp reduction (one conversion) in the FP32 kernel.
+    if (sizeof(T) == 8) {
+      double t = 0.0;
+      for (int i = lane; i < nr; i += 32) t += (double)rowsum[i];
+      t = warp_sum(t);
+      if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = t;
+    } else {
+      T t = T(0);
+      for (int i = lane; i < nr; i += 32) t += rowsum[i];
+      t = warp_sum(t);
+      if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = (double)t;
+    }
   }
 }
 
