@@ -117,6 +117,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(seconds, ws, device="cuda"):
+    """The job's time is the slowest replica's: MAX over ranks (identity at
+    ws == 1).  `device` is the tensor device of the process group's backend."""
+    if ws <= 1:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput: units every replica processed / the job's time."""
+    return ws * units_per_rank / seconds
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -257,12 +273,8 @@ def run_batch(args):
         torch.cuda.synchronize()
     launches = fr.fram_kernel_launches(ctx) - l0
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = ws * args.steps * len(pairs) / total_s
+    total_s = max_over_ranks(sum(ms) / 1e3, ws)
+    value = job_rate(args.steps * len(pairs), ws, total_s)
     # End to end with host buffers (pinned): packing, copies and unpacking inside.
     Ah = [torch.from_numpy(g.A).pin_memory().numpy() for g in pairs]
     Bh = [torch.from_numpy(g.B).pin_memory().numpy() for g in pairs]
@@ -460,13 +472,10 @@ def run_ours(args):
     with ClockSampler(dev) as clk:
         ms, infos, X, P, launches = time_solves(fr, torch, ctx, n, A, B, params, args.steps,
                                                 args.warmup, flush, node)
-    total_s = sum(ms) / 1e3
+    total_s = max_over_ranks(sum(ms) / 1e3, ws)
     if ws > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
         torch.distributed.barrier()
-    value = ws * args.steps / total_s
+    value = job_rate(args.steps, ws, total_s)
 
     # The FP64 path on the same input: the comparison the metric asks for
     # (mixed vs FP64 at equal accuracy).
@@ -496,12 +505,8 @@ def run_ours(args):
             node[1].copy_(Fh, non_blocking=True)
             node[2].copy_(Fth, non_blocking=True)
         solve_step(fr, ctx, n, Ah, Bh, params, Xh, Ph, node)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, ws)
+    e2e = {"value": job_rate(1, ws, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 2 * n * n * 8 + node_h2d, "d2h_bytes_per_step": n * n * 8 + n * 4}
 
     if rank == 0:
