@@ -183,6 +183,72 @@ def sdsn(X, theta, gamma_tol=1e-14, max_sweeps=200, keep_history=False):
 
 
 # --------------------------------------------------------------------------
+# Eq. 4 / Thm. 1: the FRA solution itself, D_X^theta = argmin over D_n of
+# ||D - (theta/2) X/max(X)||_F, which SDSN approximates (reading (iv)).  Not
+# the paper's algorithm: an exact variant of step 6.
+#
+# With Y0 = (theta/2) X/max(X), the KKT conditions of this QP read
+#   D = max(0, Y0 - a 1^T - 1 b^T),  D 1 = 1,  D^T 1 = 1
+# for some multipliers a, b; any such D is the (unique) projection.  The
+# multipliers come from block coordinate ascent on the concave dual: with b
+# fixed, each a_i solves  sum_j max(0, Y0_ij - b_j - a_i) = 1, the threshold
+# of a Euclidean projection onto the simplex (sort the row, find the
+# largest k whose k-th value exceeds (sum of the first k - 1)/k); then each
+# b_j likewise with a fixed.  `omega` > 1 over-relaxes both updates (falling
+# back to 1 as soon as the residual grows); omega = 1 is the plain method.
+# --------------------------------------------------------------------------
+@dataclass
+class FRAResult:
+    D: np.ndarray
+    sweeps: int
+    residual: float      # max |row or column sum - 1| of D
+    converged: bool
+    a: np.ndarray
+    b: np.ndarray
+
+
+def simplex_thresholds(Z):
+    """t_i with sum_j max(0, Z_ij - t_i) = 1 for every row i of Z."""
+    Zs = -np.sort(-Z, axis=1)
+    cs = np.cumsum(Zs, axis=1)
+    k = np.arange(1, Z.shape[1] + 1)
+    t = (cs - 1.0) / k
+    active = Zs > t                     # true for k = 1 .. k*, false after
+    kstar = active.sum(axis=1)          # >= 1: the largest value always qualifies
+    return t[np.arange(Z.shape[0]), kstar - 1]
+
+
+def fra_residual(D):
+    return max(float(np.max(np.abs(D.sum(axis=1) - 1.0))),
+               float(np.max(np.abs(D.sum(axis=0) - 1.0))))
+
+
+def fra_exact(X, theta, tol=1e-12, max_sweeps=10000, omega=1.0):
+    n = X.shape[0]
+    m = float(np.max(X))
+    if not m > 0:
+        raise DegenerateError("max(X) <= 0 in the FRA scaling")
+    Y0 = (theta / 2.0) * (X / m)
+    a = np.zeros(n)
+    b = np.zeros(n)
+    res, prev, w = math.inf, math.inf, 1.0
+    k = 0
+    while k < max_sweeps:
+        an = simplex_thresholds(Y0 - b[None, :])
+        a = an if k == 0 else a + w * (an - a)
+        bn = simplex_thresholds((Y0 - a[:, None]).T)
+        b = bn if k == 0 else b + w * (bn - b)
+        k += 1
+        res = fra_residual(np.maximum(0.0, Y0 - a[:, None] - b[None, :]))
+        if res <= tol:
+            break
+        w = omega if res < prev else 1.0
+        prev = res
+    D = np.maximum(0.0, Y0 - a[:, None] - b[None, :])
+    return FRAResult(D, k, res, res <= tol, a, b)
+
+
+# --------------------------------------------------------------------------
 # Alg. 1 steps 7-8: damped update and the normalized Frobenius criterion
 # (appendix, "Convergence Criterion of the Matching algorithm").
 # --------------------------------------------------------------------------
@@ -301,7 +367,12 @@ class FramResult:
 #   objective and matching error on the unscaled inputs.
 # --------------------------------------------------------------------------
 def fram(A, B, K=None, lam=1.0, alpha=0.95, theta=10.0, delta_tol=1e-6, max_outer=100,
-         gamma_tol=1e-14, max_sweeps=200, validate_inputs=True):
+         gamma_tol=1e-14, max_sweeps=200, validate_inputs=True, projection="sdsn",
+         exact_tol=None, omega=1.0):
+    """projection="sdsn" is Alg. 1 as printed; "exact" replaces step 6 by the
+    exact FRA solution (fra_exact, stopped at exact_tol, default
+    max(gamma_tol, 8 n eps), after at most max_sweeps sweeps); its residual
+    stands in for gamma in the result."""
     A0 = np.asarray(A, dtype=np.float64)
     B0 = np.asarray(B, dtype=np.float64)
     K0 = None if K is None else np.asarray(K, dtype=np.float64)
@@ -318,11 +389,17 @@ def fram(A, B, K=None, lam=1.0, alpha=0.95, theta=10.0, delta_tol=1e-6, max_oute
     t = 0
     while t < max_outer:
         X = gradient(As, N, Bs, Ks, lam)
-        res = sdsn(X, theta, gamma_tol, max_sweeps)
+        if projection == "exact":
+            tol = exact_tol if exact_tol is not None else max(gamma_tol, 8 * n * 2.0 ** -52)
+            res = fra_exact(X, theta, tol, max_sweeps, omega)
+            g = res.residual
+        else:
+            res = sdsn(X, theta, gamma_tol, max_sweeps)
+            g = res.gamma
         N, delta = damped_update(N, res.D, alpha)
         t += 1
         total += res.sweeps
-        g, conv = res.gamma, res.converged
+        conv = res.converged
         sweeps.append(res.sweeps)
         deltas.append(delta)
         if delta <= delta_tol:

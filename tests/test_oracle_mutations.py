@@ -82,3 +82,36 @@ def test_sdsn_lagged_gamma_mutant_fails_golden():
         Y = o.p2(o.p1(Y))
         k += 1
     assert k != o.sdsn(X, 10.0, 1e-14, 200).sweeps
+
+
+def _thresholds_ok(thr):
+    rng = np.random.default_rng(3)
+    Z = rng.normal(size=(12, 9))
+    t = thr(Z)
+    return np.max(np.abs(np.maximum(0.0, Z - t[:, None]).sum(1) - 1.0)) <= 1e-12
+
+
+def _thr_off_by_one(Z):      # k* - 1 used as the count of the active set
+    Zs = -np.sort(-Z, axis=1)
+    cs = np.cumsum(Zs, axis=1)
+    k = np.arange(1, Z.shape[1] + 1)
+    t = (cs - 1.0) / k
+    kstar = np.maximum((Zs > t).sum(axis=1) - 1, 1)
+    return t[np.arange(Z.shape[0]), kstar - 1]
+
+
+def _thr_no_sort(Z):         # prefix sums of the unsorted row
+    cs = np.cumsum(Z, axis=1)
+    k = np.arange(1, Z.shape[1] + 1)
+    t = (cs - 1.0) / k
+    kstar = (Z > t).sum(axis=1)
+    return t[np.arange(Z.shape[0]), kstar - 1]
+
+
+def test_reference_thresholds_pass():
+    assert _thresholds_ok(o.simplex_thresholds)
+
+
+@pytest.mark.parametrize("mutant", [_thr_off_by_one, _thr_no_sort])
+def test_threshold_mutants_fail_their_pin(mutant):
+    assert not _thresholds_ok(mutant)

@@ -468,6 +468,112 @@ def test_attributed_pair_node_term_helps():
     assert o.accuracy(r.perm, g.truth) >= 0.95
 
 
+# ------------------------------------------------ exact FRA projection (step 6 variant)
+def test_simplex_thresholds_against_bisection():
+    # sum_j max(0, z_j - t) = 1 solved by bisection on the decreasing
+    # piecewise-linear left side: an independent computation of t.
+    rng = np.random.default_rng(5)
+    Z = rng.normal(size=(20, 13)) * rng.choice([0.1, 1.0, 10.0], size=(20, 1))
+    t = o.simplex_thresholds(Z)
+    for i in range(Z.shape[0]):
+        lo, hi = Z[i].max() - 1.0, Z[i].max()        # f(lo) >= 0 >= f(hi)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if np.maximum(0.0, Z[i] - mid).sum() >= 1.0:
+                lo = mid
+            else:
+                hi = mid
+        assert abs(t[i] - 0.5 * (lo + hi)) <= 1e-12 * max(1.0, abs(t[i]))
+        assert abs(np.maximum(0.0, Z[i] - t[i]).sum() - 1.0) <= 1e-12
+
+
+@pytest.mark.parametrize("n,theta,seed", [(6, 10.0, 0), (30, 10.0, 1), (30, 2.0, 2), (80, 10.0, 3)])
+def test_fra_exact_kkt_certificate(n, theta, seed):
+    # D = max(0, Y0 - a 1^T - 1 b^T) with unit row and column sums satisfies
+    # the KKT conditions of the convex QP, so it is the projection; this
+    # certificate does not depend on how a and b were found.
+    X = rand_mat(n, 200 + seed)
+    r = o.fra_exact(X, theta, tol=1e-12)
+    assert r.converged and r.residual <= 1e-12
+    Y0 = (theta / 2.0) * (X / X.max())
+    assert np.array_equal(r.D, np.maximum(0.0, Y0 - r.a[:, None] - r.b[None, :]))
+    assert np.all(r.D >= 0)
+    assert np.max(np.abs(r.D.sum(1) - 1)) <= 1e-12 and np.max(np.abs(r.D.sum(0) - 1)) <= 1e-12
+
+
+def test_fra_exact_equals_dykstra_and_qp():
+    for seed in range(3):
+        n, theta = 5, 10.0
+        X = rand_mat(n, 300 + seed)
+        Xhat = X / X.max()
+        D = o.fra_exact(X, theta, tol=1e-14).D
+        assert np.max(np.abs(D - dykstra_ds_projection(theta / 2 * Xhat))) < 1e-9
+        D_qp = slsqp_fra(Xhat, theta)
+        assert abs(fra_value(D, Xhat, theta) - fra_value(D_qp, Xhat, theta)) < 1e-7
+        assert fra_value(D, Xhat, theta) >= fra_value(D_qp, Xhat, theta) - 1e-12
+
+
+def test_fra_exact_is_p1_when_nothing_clamps():
+    # Y0 large and flat enough that P1(Y0) >= 0: the affine projection is
+    # already in D_n, so it is the exact projection (one SDSN sweep too).
+    n, theta = 7, 10.0
+    X = 1.0 + 0.01 * rand_mat(n, 7)
+    Y0 = theta / 2 * X / X.max()
+    P1 = kkt_affine_projection(Y0)
+    assert np.all(P1 > 0)
+    r = o.fra_exact(X, theta, tol=1e-14)
+    assert np.max(np.abs(r.D - P1)) < 1e-12
+    assert np.max(np.abs(o.sdsn(X, theta, 1e-14, 1).D - r.D)) < 1e-12
+
+
+def test_fra_exact_limits_in_theta():
+    # Thm. 4 (theta -> 0: 11^T/n) and Cor. of Thm. 3 (theta -> inf: the LAP
+    # permutation, found by brute force).
+    n = 5
+    X = rand_mat(n, 21)
+    assert np.max(np.abs(o.fra_exact(X, 1e-6).D - 1.0 / n)) < 1e-6
+    perm, _ = brute_lap(X)
+    P = np.zeros((n, n))
+    P[np.arange(n), perm] = 1
+    assert np.max(np.abs(o.fra_exact(X, 1e4).D - P)) < 1e-9
+
+
+def test_fra_exact_is_closest_feasible_point():
+    # Every other doubly stochastic matrix is at least as far from Y0:
+    # permutations, the centre, Sinkhorn-balanced matrices, converged SDSN.
+    n, theta = 8, 10.0
+    X = rand_mat(n, 9)
+    Y0 = theta / 2 * X / X.max()
+    d_star = np.linalg.norm(o.fra_exact(X, theta).D - Y0)
+    rng = np.random.default_rng(1)
+    cands = [np.full((n, n), 1.0 / n), o.sdsn(X, theta, 1e-15, 100000).D]
+    for _ in range(20):
+        P = np.eye(n)[rng.permutation(n)]
+        cands.append(P)
+        M = rng.random((n, n))
+        for _ in range(200):
+            M /= M.sum(1, keepdims=True)
+            M /= M.sum(0, keepdims=True)
+        cands.append(M)
+    for D in cands:
+        assert np.linalg.norm(D - Y0) >= d_star - 1e-12
+
+
+def test_fra_exact_over_relaxation_reaches_the_same_point():
+    X = rand_mat(40, 4)
+    a = o.fra_exact(X, 10.0, tol=1e-12)
+    b = o.fra_exact(X, 10.0, tol=1e-12, omega=1.6)
+    assert np.max(np.abs(a.D - b.D)) < 1e-10
+
+
+def test_fram_exact_projection_recovers_and_is_scale_invariant():
+    g = fi.er_pair(40, 0.3, noise=0.0, seed=8, theta=10.0)
+    r = o.fram(g.A, g.B, theta=10.0, projection="exact", omega=1.6)
+    assert o.accuracy(r.perm, g.truth) == 1.0
+    r4 = o.fram(4 * g.A, 4 * g.B, theta=10.0, projection="exact", omega=1.6)
+    assert np.array_equal(r.N, r4.N) and r.outer_iters == r4.outer_iters
+
+
 def test_validation_rejects_bad_inputs():
     A = rand_mat(4, 1, asym=False)
     with pytest.raises(o.InvalidInputError):
