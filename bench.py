@@ -458,6 +458,9 @@ def run_ours(args):
     mixed = args.precision != "fp64"
     params = fr.fram_default_params(theta=g.theta, precision=PRECISIONS[args.precision],
                                     max_polish=args.polish if mixed else 0)
+    if args.projection == "exact":   # step 6 variant: the exact FRA solution (FP64 path)
+        params.projection = fr.FRAM_PROJ_EXACT
+        params.max_sweeps = args.exact_sweeps
     A = torch.from_numpy(g.A).to("cuda")
     B = torch.from_numpy(g.B).to("cuda")
     node = None
@@ -521,6 +524,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": desc, "n": n, "precision": args.precision,
+                       "projection": args.projection,
                        "fp64_polish_sweeps": params.max_polish,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -625,6 +629,10 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--polish", type=int, default=4, help="FP64 polish sweeps (mixed paths)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--projection", choices=["sdsn", "exact"], default="sdsn",
+                    help="step 6: the paper's SDSN or the exact FRA projection (fp64 only)")
+    ap.add_argument("--exact-sweeps", type=int, default=2000,
+                    help="sweep cap of the exact projection")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -62,6 +62,16 @@ typedef enum {
   FRAM_PREC_MIXED_BF16 = 2  /* BF16 tensor-core gradient, FP32 SDSN, FP64 update    */
 } fram_precision;
 
+/* Step 6 projection.  FRAM_PROJ_SDSN is Alg. 2 as printed (alternating
+ * projections, stopped by gamma or the sweep cap).  FRAM_PROJ_EXACT computes
+ * the FRA solution of eq. 4 / Thm. 1 exactly (not in the paper: multipliers
+ * a, b with D = max(0, Y0 - a 1^T - 1 b^T) by dual block coordinate ascent,
+ * see fram_fra_exact); FP64 path only. */
+typedef enum {
+  FRAM_PROJ_SDSN = 0,
+  FRAM_PROJ_EXACT = 1
+} fram_projection;
+
 /* Solver parameters.  fram_default_params() fills the paper's settings
  * (Sec. 7 "Setting": lambda = 1, alpha = 0.95, theta = 10 for sparse graphs;
  * use theta = 2 for dense ones) and the tolerances and caps that the paper
@@ -85,7 +95,9 @@ typedef struct {
   int max_polish;     /* mixed paths: FP64 polish sweep cap per call (default 0)    */
   int precision;      /* fram_precision                                             */
   int init;           /* 0 = auto (N0 = 0 with K, 11^T/n without), 1 = zero, 2 = uniform */
-  int reserved;       /* must be 0                                                  */
+  int projection;     /* fram_projection (default FRAM_PROJ_SDSN).  EXACT stops at a */
+                      /* row residual <= max(gamma_tol, 8 n eps), at most max_sweeps */
+                      /* sweeps; its residual is reported as gamma                   */
 } fram_params;
 
 /* Per-solve diagnostics (all optional to read). */
@@ -230,6 +242,19 @@ fram_status fram_gradient_lowp(fram_ctx *ctx, int n, const double *A, const doub
  * FRAM_ERR_DEGENERATE if max(X) <= 0. */
 fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double theta,
                       double gamma_tol, int max_sweeps, int *sweeps_out, double *gamma_out);
+
+/* Exact FRA projection (eq. 4 / Thm. 1; a variant of Alg. 1 step 6, not in
+ * the paper): D = argmin over doubly stochastic D of ||D - (theta/2) X/max X||_F,
+ * computed as D = max(0, Y0 - a 1^T - 1 b^T) by block coordinate ascent on
+ * the dual (each multiplier the exact root of its piecewise-linear equation,
+ * over-relaxed while the residual falls), in FP64.  X, D: n x n device
+ * arrays (D may equal X), n <= 12800.  Stops at the first point whose row
+ * residual max_i |sum_j D_ij - 1| is <= tol and whose column multipliers
+ * came from a plain step (column sums exact up to rounding), or after
+ * max_sweeps sweeps.  sweeps_out and res_out (host) may be NULL.
+ * FRAM_ERR_DEGENERATE if max(X) <= 0. */
+fram_status fram_fra_exact(fram_ctx *ctx, int n, const double *X, double *D, double theta,
+                           double tol, int max_sweeps, int *sweeps_out, double *res_out);
 
 /* SDSN (as fram_sdsn) of `count` independent problems in ONE grouped,
  * cooperative launch: problem i (size n[i], device X[i] -> D[i]) runs on the

@@ -30,6 +30,8 @@ FRAM_ERR_BUSY = -6
 FRAM_PREC_FP64 = 0
 FRAM_PREC_MIXED_TF32 = 1
 FRAM_PREC_MIXED_BF16 = 2
+FRAM_PROJ_SDSN = 0
+FRAM_PROJ_EXACT = 1
 
 STATUS_NAMES = {0: "FRAM_OK", 1: "FRAM_NOT_READY", -1: "FRAM_ERR_INVALID", -2: "FRAM_ERR_OOM",
                 -3: "FRAM_ERR_CUDA", -4: "FRAM_ERR_DEGENERATE", -5: "FRAM_ERR_TIMEOUT",
@@ -41,7 +43,7 @@ class FramParams(C.Structure):
                 ("delta_tol", C.c_double), ("gamma_tol", C.c_double), ("polish_tol", C.c_double),
                 ("mixed_delta_tol", C.c_double), ("stall_ratio", C.c_double),
                 ("stall_below", C.c_double), ("max_outer", C.c_int), ("max_sweeps", C.c_int), ("max_polish", C.c_int),
-                ("precision", C.c_int), ("init", C.c_int), ("reserved", C.c_int)]
+                ("precision", C.c_int), ("init", C.c_int), ("projection", C.c_int)]
 
 
 class FramInfo(C.Structure):
@@ -92,6 +94,7 @@ def load(path: str | None = None):
         "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
         "fram_node_affinity": (i, [_P, i, i, _P, _P, _P]),
+        "fram_fra_exact": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
@@ -112,7 +115,7 @@ def exported_symbols():
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
             "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_node_affinity", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
+            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
 
@@ -294,6 +297,16 @@ def fram_sdsn_grouped(ctx, ns, Xs, Ds, theta, gamma_tol=1e-14, max_sweeps=200, c
     if check:
         _check(ctx, st)
     return st, list(sw), list(g)
+
+
+def fram_fra_exact(ctx, n, X, D, theta, tol=1e-12, max_sweeps=10000, check=True):
+    sw = C.c_int()
+    res = C.c_double()
+    st = load().fram_fra_exact(ctx, n, _addr(X), _addr(D), theta, tol, max_sweeps, C.byref(sw),
+                               C.byref(res))
+    if check:
+        _check(ctx, st)
+    return st, sw.value, res.value
 
 
 def fram_assign(ctx, n, W, perm, check=True, with_phases=False):

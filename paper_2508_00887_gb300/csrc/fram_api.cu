@@ -149,14 +149,26 @@ fram_status ensure_mixed(fram_ctx* c, int n) {
   return FRAM_OK;
 }
 
+// Stop tolerance of the exact projection: the requested gamma_tol, but not
+// below what FP64 row sums of n terms can resolve.
+double exact_tol(double gamma_tol, int n) {
+  const double floor_tol = 8.0 * n * 2.220446049250313e-16;
+  return gamma_tol > floor_tol ? gamma_tol : floor_tol;
+}
+
 fram_status check_params(fram_ctx* c, const fram_params& p) {
   if (!(p.alpha > 0.0 && p.alpha <= 1.0) || !(p.theta > 0.0) || !isfinite(p.theta) ||
       !isfinite(p.lambda) || !(p.delta_tol >= 0.0) || !(p.gamma_tol == p.gamma_tol) ||
       !(p.stall_ratio >= 0.0 && p.stall_ratio <= 1.0) || !(p.stall_below >= 0.0) ||
       !(p.mixed_delta_tol >= 0.0) ||
       p.max_outer < 1 || p.max_sweeps < 1 || p.max_polish < 0 || p.init < 0 || p.init > 2 ||
-      p.precision < FRAM_PREC_FP64 || p.precision > FRAM_PREC_MIXED_BF16 || p.reserved != 0) {
+      p.precision < FRAM_PREC_FP64 || p.precision > FRAM_PREC_MIXED_BF16 ||
+      p.projection < FRAM_PROJ_SDSN || p.projection > FRAM_PROJ_EXACT) {
     set_err(c, "invalid fram_params");
+    return FRAM_ERR_INVALID;
+  }
+  if (p.projection == FRAM_PROJ_EXACT && p.precision != FRAM_PREC_FP64) {
+    set_err(c, "the exact projection runs on the FP64 path only");
     return FRAM_ERR_INVALID;
   }
   return FRAM_OK;
@@ -290,21 +302,30 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
                              &w.scal->xmax_key, c->stream),
                 "gemm");
       FR_CUDA(cudaEventRecord(c->evp[1], c->stream), "event");
-      SdsnLaunch L{};
-      L.n = n;
-      L.X = w.X;
-      L.ldx = ld;
-      L.Y = w.X;
-      L.ldy = ld;
-      L.theta = p.theta;
-      L.gamma_tol = p.gamma_tol;
-      L.max_sweeps = p.max_sweeps;
-      L.xmax_key = &w.scal->xmax_key;
-      L.stats = &w.scal->iter.sdsn;
-      L.partials = w.sdsn_partials;
-      L.barrier = &w.scal->bar;
-      L.limit_ns = c->wait_limit_ns;
-      FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+      if (p.projection == FRAM_PROJ_EXACT) {
+        // Step 6 variant: the exact FRA solution (T is free after the GEMMs).
+        FR_LAUNCH(launch_fra(w.X, ld, w.T, ld, n, &w.scal->xmax_key, p.theta,
+                             exact_tol(p.gamma_tol, n), p.max_sweeps, w.sdsn_partials,
+                             &w.scal->bar, &w.scal->iter.sdsn, c->wait_limit_ns, c->num_sms,
+                             c->stream),
+                  "exact projection kernel");
+      } else {
+        SdsnLaunch L{};
+        L.n = n;
+        L.X = w.X;
+        L.ldx = ld;
+        L.Y = w.X;
+        L.ldy = ld;
+        L.theta = p.theta;
+        L.gamma_tol = p.gamma_tol;
+        L.max_sweeps = p.max_sweeps;
+        L.xmax_key = &w.scal->xmax_key;
+        L.stats = &w.scal->iter.sdsn;
+        L.partials = w.sdsn_partials;
+        L.barrier = &w.scal->bar;
+        L.limit_ns = c->wait_limit_ns;
+        FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+      }
       FR_CUDA(cudaEventRecord(c->evp[2], c->stream), "event");
       FR_LAUNCH(launch_update(w.N, ld, w.X, ld, n, p.alpha, &w.scal->iter, w.partials,
                               &w.scal->ticket_update, c->stream),
@@ -389,7 +410,7 @@ void fram_default_params(fram_params* p) {
   p->max_polish = 0;
   p->precision = FRAM_PREC_FP64;
   p->init = 0;
-  p->reserved = 0;
+  p->projection = FRAM_PROJ_SDSN;
 }
 
 fram_status fram_create(fram_ctx** out, int device, size_t budget, void* stream) {
@@ -620,6 +641,45 @@ fram_status fram_sdsn(fram_ctx* c, int n, const double* X, double* D, double the
   FR_TRY(dev_status(c, st.status, "SDSN"));
   if (sweeps_out) *sweeps_out = st.sweeps;
   if (gamma_out) *gamma_out = st.gamma;
+  return FRAM_OK;
+}
+
+fram_status fram_fra_exact(fram_ctx* c, int n, const double* X, double* D, double theta,
+                           double tol, int max_sweeps, int* sweeps_out, double* res_out) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || !X || !D || !is_device_ptr(X) || !is_device_ptr(D) || !(theta > 0.0) ||
+      !isfinite(theta) || max_sweeps < 1 || !(tol >= 0.0)) {
+    set_err(c, "fram_fra_exact: n >= 1, device X and D, theta > 0, tol >= 0, max_sweeps >= 1");
+    return FRAM_ERR_INVALID;
+  }
+  if (2 * (size_t)n * sizeof(double) > 200 * 1024) {
+    set_err(c, "fram_fra_exact: n = %d exceeds the limit of 12800", n);
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  FR_LAUNCH(launch_scale(X, n, 1.0, false, w.X, ld, c->stream), "copy");
+  FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream), "memset");
+  FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
+  FR_LAUNCH(launch_max(w.X, ld, n, &w.scal->xmax_key, c->stream), "max kernel");
+  FR_LAUNCH(launch_fra(w.X, ld, w.T, ld, n, &w.scal->xmax_key, theta, tol, max_sweeps,
+                       w.sdsn_partials, &w.scal->bar, &w.scal->iter.sdsn, c->wait_limit_ns,
+                       c->num_sms, c->stream),
+            "exact projection kernel");
+  FR_CUDA(cudaMemcpy2DAsync(D, (size_t)n * sizeof(double), w.X, (size_t)ld * sizeof(double),
+                            (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, c->stream),
+          "copy D");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.sdsn, &w.scal->iter.sdsn, sizeof(SdsnStats),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  const SdsnStats& st = w.hscal->iter.sdsn;
+  FR_TRY(dev_status(c, st.status, "exact projection"));
+  if (sweeps_out) *sweeps_out = st.sweeps;
+  if (res_out) *res_out = st.gamma;
   return FRAM_OK;
 }
 

@@ -956,6 +956,10 @@ extern "C" fram_status fram_solve_batched(fram_ctx* c, int count, const int* n,
   {
     fram_status st = check_params(c, p);
     if (st != FRAM_OK) return st;
+    if (p.projection != FRAM_PROJ_SDSN) {
+      set_err(c, "fram_solve_batched: the exact projection is available through fram_solve only");
+      return FRAM_ERR_INVALID;
+    }
   }
   for (int i = 0; i < count; ++i)
     if (n[i] < 1 || !A[i] || !B[i] || !perm_out[i]) {

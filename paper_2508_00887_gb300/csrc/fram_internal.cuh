@@ -119,6 +119,39 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b, unsigned nblocks, unsi
   return *s_flag != 0;
 }
 
+// Barrier on a counter that only grows: the k-th barrier of the launch waits
+// until the counter reaches k * nblocks.  Time-limited (see GridBarrier).
+__device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
+                                                uint64_t limit_ns, int* status, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    // The barrier above orders the CTA's writes before thread 0's release.
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
+    if ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+      const uint64_t t0 = globaltimer_ns();
+      unsigned polls = 0;
+      while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
+        if ((++polls & 63u) == 0) {
+          if (ld_volatile_s32(&b->abort)) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer_ns() - t0 > limit_ns) {
+            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+            atomicExch(&b->abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
 // ------------------------------------------------------------ SDSN state
 struct SdsnStats {
   int sweeps;
@@ -193,6 +226,13 @@ struct SdsnLaunch {
   uint64_t limit_ns;
 };
 size_t sdsn_partials_elems(int n, int max_blocks);
+// Exact FRA projection (FP64): Y holds X on entry and D on return (ld-strided),
+// Yt is n x n scratch, ws holds fra_workspace_elems doubles.  stats->gamma
+// gets the row residual max_i |sum_j D_ij - 1| of the returned D.
+size_t fra_workspace_elems(int n, int num_sms);
+int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned long long* xmax_key,
+               double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
+               SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 // Several problems (same precision pair) in one cooperative launch of at most

@@ -82,39 +82,6 @@ __device__ __forceinline__ float relu(float y) {
   return __int_as_float(b & ~(b >> 31));
 }
 
-// Barrier on a counter that only grows: the k-th barrier of the launch waits
-// until the counter reaches k * nblocks.  Time-limited (see GridBarrier).
-__device__ __forceinline__ bool grid_sync_epoch(GridBarrier* b, unsigned target,
-                                                uint64_t limit_ns, int* status, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    // The barrier above orders the CTA's writes before thread 0's release.
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
-    if ((int)(ld_acquire_u32(&b->count) - target) < 0) {
-      const uint64_t t0 = globaltimer_ns();
-      unsigned polls = 0;
-      while ((int)(ld_acquire_u32(&b->count) - target) < 0) {
-        if ((++polls & 63u) == 0) {
-          if (ld_volatile_s32(&b->abort)) {
-            ok = 0;
-            break;
-          }
-          if (globaltimer_ns() - t0 > limit_ns) {
-            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-            atomicExch(&b->abort, 1);
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
 // VEC consecutive elements of U at p: one 16/8/4-byte access when `vec`
 // (the address is then VEC*sizeof(U)-aligned), element by element otherwise
 // or when the vector would cross `lim` (elements valid: p[0 .. lim-1]).

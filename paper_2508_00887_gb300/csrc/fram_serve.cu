@@ -513,6 +513,10 @@ extern "C" fram_status fram_submit(fram_ctx* c, int n, const double* A, const do
     fram_default_params(&p);
   fram_status st = check_params(c, p);
   if (st != FRAM_OK) return st;
+  if (p.projection != FRAM_PROJ_SDSN) {
+    set_err(c, "fram_submit: the exact projection is available through fram_solve only");
+    return FRAM_ERR_INVALID;
+  }
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "set device");
   st = FRAM_OK;
   Serve* S = get_serve(c, &st);

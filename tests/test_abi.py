@@ -70,7 +70,7 @@ int main(void) {{
     ("fram_params", fr.FramParams,
      ["lambda", "alpha", "theta", "delta_tol", "gamma_tol", "polish_tol", "mixed_delta_tol",
       "stall_ratio", "stall_below", "max_outer",
-      "max_sweeps", "max_polish", "precision", "init", "reserved"]),
+      "max_sweeps", "max_polish", "precision", "init", "projection"]),
     ("fram_info", fr.FramInfo,
      ["outer_iters", "total_sweeps", "polish_sweeps", "sdsn_converged_last", "lap_augmentations",
       "lap_auction_phases", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total",
