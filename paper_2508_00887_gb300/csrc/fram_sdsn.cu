@@ -133,9 +133,9 @@ __device__ __forceinline__ void vec_store(U* p, bool vec, int lim, const U (&in)
 // sums in shared memory.
 template <typename T, typename TIn, int MAXC, bool FIRST>
 __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int ldt, T* colacc,
-                                          T* rowsum, const T* arow, const T* bcol, int nr,
+                                          T* rowsum, T* arow, T* bcol, int nr,
                                           int nc, int r0, int c0, int bi, int bj, T scale, int wb,
-                                          int blk, int nblk, T cS) {
+                                          int blk, int nblk, T cS, T inv_n_t, double* s_total) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T* wacc = colacc + warp * p.tc;
   if constexpr (MAXC == 0) {
@@ -234,8 +234,18 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
     }
   }
   __syncthreads();
+  // A problem on one CTA keeps its sums on chip: the next sweep's row and
+  // column terms and the total go straight to shared memory (the same values
+  // the gather below would produce).  Otherwise they are published as
+  // partials for the other CTAs.
+  const bool local = nblk == 1;
   T* rp = p.rpart + ((size_t)wb * p.Q + bj) * p.n + r0;
-  for (int i = tid; i < nr; i += kSdsnThreads) rp[i] = rowsum[i];
+  for (int i = tid; i < nr; i += kSdsnThreads) {
+    if (local)
+      arow[i] = inv_n_t - rowsum[i] * inv_n_t;
+    else
+      rp[i] = rowsum[i];
+  }
   // Column sums: four threads per column add four warps' values each, then
   // combine with two shuffles (a fixed order).
   T* cp = p.cpart + ((size_t)wb * p.P + bi) * p.n + c0;
@@ -248,7 +258,12 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
     }
     c += __shfl_xor_sync(0xffffffffu, c, 1);
     c += __shfl_xor_sync(0xffffffffu, c, 2);
-    if (part == 0 && j < nc) cp[j] = c;
+    if (part == 0 && j < nc) {
+      if (local)
+        bcol[j] = c * inv_n_t;
+      else
+        cp[j] = c;
+    }
   }
   if (warp == 0) {
     // Tile total for S: FP64 in the FP64 kernel; from the FP32 row sums in
@@ -257,12 +272,22 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
       double t = 0.0;
       for (int i = lane; i < nr; i += 32) t += (double)rowsum[i];
       t = warp_sum(t);
-      if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = t;
+      if (lane == 0) {
+        if (local)
+          *s_total = t;
+        else
+          p.tpart[(size_t)wb * nblk + blk] = t;
+      }
     } else {
       T t = T(0);
       for (int i = lane; i < nr; i += 32) t += rowsum[i];
       t = warp_sum(t);
-      if (lane == 0) p.tpart[(size_t)wb * nblk + blk] = (double)t;
+      if (lane == 0) {
+        if (local)
+          *s_total = (double)t;
+        else
+          p.tpart[(size_t)wb * nblk + blk] = (double)t;
+      }
     }
   }
 }
@@ -272,7 +297,7 @@ template <typename T, typename TIn, int MAXC>
 __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int nblk,
                                           unsigned char* smem) {
   __shared__ int s_flag, s_stop;
-  __shared__ double s_g;
+  __shared__ double s_g, s_total;
   __shared__ T s_cS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bi = blk / p.Q, bj = blk % p.Q;
@@ -321,9 +346,13 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
   const T scale = (T)((p.theta / 2.0) / m);
 
   sdsn_pass<T, TIn, MAXC, true>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi, bj,
-                                scale, 0, blk, nblk, T(0));
+                                scale, 0, blk, nblk, T(0), inv_n_t, &s_total);
   unsigned epoch = 1;
-  if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
+  if (nblocks > 1) {
+    if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
+  } else {
+    __syncthreads();
+  }
 
   double g = INFINITY;
   int k = 0;
@@ -334,8 +363,12 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
     // warp 0 (FP64 instructions are scarce on this GPU).
     if (warp == 0) {
       double s = 0.0;
-      for (unsigned t = lane; t < nblocks; t += 32) s += __ldcg(&p.tpart[(size_t)rb * nblocks + t]);
-      s = warp_sum(s);
+      if (nblocks > 1) {
+        for (unsigned t = lane; t < nblocks; t += 32) s += __ldcg(&p.tpart[(size_t)rb * nblocks + t]);
+        s = warp_sum(s);
+      } else {
+        s = s_total;
+      }
       if (lane == 0) {
         const double gk = s * inv_n - 1.0;
         s_g = gk;
@@ -343,7 +376,7 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
         s_cS = (T)(s * inv_n2);
       }
     }
-    for (int e = tid; e < nr + nc; e += kSdsnThreads) {
+    for (int e = tid; e < (nblocks > 1 ? nr + nc : 0); e += kSdsnThreads) {
       const bool is_row = e < nr;
       const int idx = is_row ? e : e - nr;
       const int cnt = is_row ? p.Q : p.P;
@@ -367,10 +400,14 @@ __device__ __forceinline__ void sdsn_body(const SdsnK<T, TIn>& p, int blk, int n
     if (s_stop) break;
     if (k >= max_sweeps) break;
     sdsn_pass<T, TIn, MAXC, false>(p, tile, ldt, colacc, rowsum, arow, bcol, nr, nc, r0, c0, bi,
-                                   bj, scale, rb ^ 1, blk, nblk, s_cS);
+                                   bj, scale, rb ^ 1, blk, nblk, s_cS, inv_n_t, &s_total);
     ++k;
     ++epoch;
-    if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
+    if (nblocks > 1) {
+      if (!grid_sync_epoch(p.bar, epoch * nblocks, p.limit_ns, status, &s_flag)) return;
+    } else {
+      __syncthreads();
+    }
   }
 
   if (p.resident) {
