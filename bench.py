@@ -42,6 +42,9 @@ WORKLOADS = {
                fi.medium_er_pair),
     "large": ("Gaussian-kernel pair n=8192, sigma=median distance, N(0,0.01) jitter, theta=2",
               fi.large_gaussian_pair),
+    "social": ("Facebook-sized power-law social pair: Chung-Lu graph, n=4039, ~88k unweighted "
+               "edges, degree exponent 3.1, planted relabelling, 5% edge flips, theta=10",
+               fi.facebook_like_pair),
     "attributed": ("Gaussian-kernel pair n=1000 with d=128 nonnegative unit node descriptors "
                    "(N(0,0.5/sqrt(d)) noise on the partner), K = F F~^T computed in the step, "
                    "theta=2, lambda=1", fi.attributed_medium_pair),

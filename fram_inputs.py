@@ -105,6 +105,51 @@ def er_pair(n: int, p: float, noise: float = 0.0, flip_frac: float = 0.0,
                      dict(kind="er", n=n, p=p, noise=noise, flip_frac=flip_frac, seed=seed))
 
 
+def _flip_binary_edges(B: np.ndarray, flip_frac: float, rng: np.random.Generator) -> np.ndarray:
+    """Delete flip_frac of the edges of a 0/1 graph and add as many new ones."""
+    n = B.shape[0]
+    iu = np.triu_indices(n, 1)
+    vals = B[iu].copy()
+    on = np.flatnonzero(vals > 0)
+    off = np.flatnonzero(vals == 0)
+    k = min(int(round(flip_frac * on.size)), off.size)
+    if k > 0:
+        vals[rng.choice(on, size=k, replace=False)] = 0.0
+        vals[rng.choice(off, size=k, replace=False)] = 1.0
+    U = np.zeros((n, n))
+    U[iu] = vals
+    return _symmetric_from_upper(U)
+
+
+def social_pair(n: int = 4039, m: int = 88234, flip_frac: float = 0.05, seed: int = 0,
+                exponent: float = 3.1, theta: float = 10.0) -> GraphPair:
+    """Unweighted social-network-like pair: a Chung-Lu graph whose expected
+    degrees follow a power law (exponent 3.1: at the default size the largest
+    degree is near 1,200 and the median near 33), scaled so the expected edge
+    count is m (n and m default to the size of the Facebook ego graph), a
+    planted relabelling, and flip_frac of the copy's edges moved at random."""
+    rng = np.random.default_rng(seed)
+    w = (np.arange(1, n + 1, dtype=np.float64)) ** (-1.0 / (exponent - 1.0))
+    w = w[rng.permutation(n)]
+    iu = np.triu_indices(n, 1)
+    scale = 1.0
+    for _ in range(50):          # fix the scale so that sum_{i<j} p_ij = m
+        ws = w * scale
+        P = np.minimum(1.0, np.outer(ws, ws) / ws.sum())
+        e = P[iu].sum()
+        if abs(e - m) <= 1e-6 * m:
+            break
+        scale *= m / e
+    U = np.zeros((n, n))
+    U[iu] = (rng.random(iu[0].size) < P[iu]).astype(np.float64)
+    A = _symmetric_from_upper(U)
+    perm = rng.permutation(n).astype(np.int64)
+    B = _flip_binary_edges(_permute(A, perm), flip_frac, rng) if flip_frac > 0 else _permute(A, perm)
+    return GraphPair(np.ascontiguousarray(A), np.ascontiguousarray(B), perm, theta,
+                     dict(kind="social", n=n, m=m, flip_frac=flip_frac, seed=seed,
+                          edges=int(U.sum())))
+
+
 def _kernel_from_points(P: np.ndarray) -> np.ndarray:
     """Gaussian-kernel adjacency exp(-d^2/sigma^2), sigma = median pairwise distance."""
     sq = np.sum(P * P, axis=1)
@@ -229,6 +274,11 @@ def medium_er_pair(seed: int = 0) -> GraphPair:
 def attributed_medium_pair(seed: int = 0) -> GraphPair:
     """n=1000 dense Gaussian-kernel pair with d=128 node descriptors, theta=2."""
     return attributed_pair(1000, d=128, seed=seed)
+
+
+def facebook_like_pair(seed: int = 0) -> GraphPair:
+    """n=4039 power-law social pair with about 88,234 edges, 5% edge flips."""
+    return social_pair(4039, 88234, 0.05, seed)
 
 
 def large_gaussian_pair(seed: int = 0, n: int = 8192) -> GraphPair:

@@ -214,6 +214,14 @@ fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *pe
 fram_status fram_gradient(fram_ctx *ctx, int n, const double *A, const double *N, const double *B,
                           const double *K, double lambda, double *X);
 
+/* FP64 path (fram_solve, fram_gradient): the gradient of eq. 3 uses CSR
+ * products for A_s and for B_s when their fraction of nonzero entries is at
+ * most max_density (default 0.2; 0 always uses the dense GEMM).  The CSR
+ * products add the same terms in the same order as the dense GEMM, so the
+ * result does not change, only the time: 2 nnz n instead of 2 n^3 flops.
+ * FRAM_ERR_INVALID outside [0, 1]. */
+fram_status fram_set_sparse_density(fram_ctx *ctx, double max_density);
+
 /* Node-attribute affinity K = F Ft^T: the node term <N, F F~^T> of eq. 1,
  * whose gradient lambda F F~^T enters eq. 3.  K[i][j] is the inner product
  * of node i's attribute vector in G with node j's in G~.

@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
         "fram_node_affinity": (i, [_P, i, i, _P, _P, _P]),
         "fram_fra_exact": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
+        "fram_set_sparse_density": (i, [_P, d]),
         "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
@@ -115,7 +116,7 @@ def exported_symbols():
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
             "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
+            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
 
@@ -297,6 +298,13 @@ def fram_sdsn_grouped(ctx, ns, Xs, Ds, theta, gamma_tol=1e-14, max_sweeps=200, c
     if check:
         _check(ctx, st)
     return st, list(sw), list(g)
+
+
+def fram_set_sparse_density(ctx, max_density, check=True):
+    st = load().fram_set_sparse_density(ctx, max_density)
+    if check:
+        _check(ctx, st)
+    return st
 
 
 def fram_fra_exact(ctx, n, X, D, theta, tol=1e-12, max_sweeps=10000, check=True):

@@ -58,8 +58,14 @@ static void dfree(void*& p) {
 void Workspace::release() {
   void** ptrs[] = {(void**)&As, (void**)&Bs, (void**)&Ks, (void**)&N, (void**)&T, (void**)&X,
                    (void**)&A0, (void**)&B0, (void**)&K0, (void**)&perm, &lap_ws,
-                   (void**)&partials, (void**)&sdsn_partials, (void**)&scal, &mixed};
+                   (void**)&partials, (void**)&sdsn_partials, (void**)&scal, &mixed,
+                   (void**)&sp_cnt, (void**)&sp_rowptr[0], (void**)&sp_rowptr[1],
+                   (void**)&sp_col[0], (void**)&sp_col[1], (void**)&sp_val[0],
+                   (void**)&sp_val[1]};
   for (void** p : ptrs) dfree(*p);
+  sp_cap_n = 0;
+  sp_cap_nnz[0] = sp_cap_nnz[1] = 0;
+  sp_on[0] = sp_on[1] = false;
   if (hscal) cudaFreeHost(hscal);
   hscal = nullptr;
   cap_n = 0;
@@ -270,6 +276,96 @@ fram_status validate_and_scale(fram_ctx* c, int n, const double* A0, const doubl
   return FRAM_OK;
 }
 
+// FP64 gradient operands in CSR when sparse enough (fraction of nonzeros at
+// most c->sparse_density): CSR of A_s and of B_s^T.  Uses T as scratch for
+// B_s^T, so it runs before the outer loop.
+fram_status prepare_sparse(fram_ctx* c, int n) {
+  Workspace& w = c->ws;
+  w.sp_on[0] = w.sp_on[1] = false;
+  if (!(c->sparse_density > 0.0) || n < 64) return FRAM_OK;
+  const int ld = round_ld(n);
+  auto grow = [&](void** p, size_t& cap, size_t need, size_t elem) -> bool {
+    if (*p && cap >= need) return true;
+    dfree(*p);
+    cap = 0;
+    if (cudaMalloc(p, (need ? need : 1) * elem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = need;
+    return true;
+  };
+  size_t capn = (size_t)w.sp_cap_n;
+  if (!grow((void**)&w.sp_cnt, capn, (size_t)n, sizeof(int))) {
+    set_err(c, "out of device memory for the sparse gradient");
+    return FRAM_ERR_OOM;
+  }
+  size_t capr0 = (size_t)w.sp_cap_n, capr1 = (size_t)w.sp_cap_n;
+  if (!grow((void**)&w.sp_rowptr[0], capr0, (size_t)n + 1, sizeof(int)) ||
+      !grow((void**)&w.sp_rowptr[1], capr1, (size_t)n + 1, sizeof(int))) {
+    set_err(c, "out of device memory for the sparse gradient");
+    return FRAM_ERR_OOM;
+  }
+  w.sp_cap_n = n;
+  const double* src[2] = {w.As, w.T};
+  FR_LAUNCH(launch_transpose(w.Bs, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "transpose");
+  int nnz[2];
+  for (int m = 0; m < 2; ++m) {
+    FR_LAUNCH(launch_csr_count(src[m], ld, n, w.sp_cnt, c->stream), "csr count");
+    FR_LAUNCH(launch_csr_scan(w.sp_cnt, n, w.sp_rowptr[m], c->stream), "csr scan");
+    FR_CUDA(cudaMemcpyAsync(&nnz[m], w.sp_rowptr[m] + n, sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream),
+            "readback");
+  }
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  for (int m = 0; m < 2; ++m) {
+    if ((double)nnz[m] > c->sparse_density * (double)n * (double)n) continue;
+    if (!w.sp_col[m] || !w.sp_val[m] || w.sp_cap_nnz[m] < (size_t)nnz[m]) {
+      // column indices and values grow together, to the same capacity
+      dfree(*(void**)&w.sp_col[m]);
+      dfree(*(void**)&w.sp_val[m]);
+      w.sp_cap_nnz[m] = 0;
+      const size_t cap = nnz[m] > 0 ? (size_t)nnz[m] : 1;
+      if (cudaMalloc((void**)&w.sp_col[m], cap * sizeof(int)) != cudaSuccess ||
+          cudaMalloc((void**)&w.sp_val[m], cap * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, "out of device memory for the sparse gradient");
+        return FRAM_ERR_OOM;
+      }
+      w.sp_cap_nnz[m] = cap;
+    }
+    FR_LAUNCH(launch_csr_fill(src[m], ld, n, w.sp_rowptr[m], w.sp_col[m], w.sp_val[m], c->stream),
+              "csr fill");
+    w.sp_on[m] = true;
+  }
+  return FRAM_OK;
+}
+
+// X = A_s N B_s (+ lam K_s) into w.X with max(X) into cmax (may be NULL):
+// dense DGEMMs, or the CSR products when prepare_sparse switched them on
+// (bit-identical results).
+fram_status fp64_gradient(fram_ctx* c, int n, bool withK, double lam, unsigned long long* cmax) {
+  Workspace& w = c->ws;
+  const int ld = round_ld(n);
+  if (w.sp_on[0])
+    FR_LAUNCH(launch_spmm(w.sp_rowptr[0], w.sp_col[0], w.sp_val[0], n, w.N, ld, w.T, c->stream),
+              "spmm");
+  else
+    FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
+  if (w.sp_on[1]) {
+    // X^T = B_s^T T^T, then X = (X^T)^T (+ lam K) with the max.
+    FR_LAUNCH(launch_transpose(w.T, w.X, ld, n, nullptr, 0.0, nullptr, c->stream), "transpose");
+    FR_LAUNCH(launch_spmm(w.sp_rowptr[1], w.sp_col[1], w.sp_val[1], n, w.X, ld, w.T, c->stream),
+              "spmm");
+    FR_LAUNCH(launch_transpose(w.T, w.X, ld, n, withK ? w.Ks : nullptr, lam, cmax, c->stream),
+              "transpose");
+  } else {
+    FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, withK ? w.Ks : nullptr, lam, cmax, c->stream),
+              "gemm");
+  }
+  return FRAM_OK;
+}
+
 // The full single-pair solve on device-resident (or staged) inputs.
 fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, const double* K,
                       const fram_params& p, double* X_out, int32_t* perm_out, fram_info* info) {
@@ -292,15 +388,13 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
   double delta = INFINITY;
   fram_status rs = FRAM_OK;
   if (p.precision == FRAM_PREC_FP64) {
+    FR_TRY(prepare_sparse(c, n));
     for (int t = 0; t < p.max_outer; ++t) {
       FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream),
               "memset");
       FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
       FR_CUDA(cudaEventRecord(c->evp[0], c->stream), "event");
-      FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
-      FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, K0 ? w.Ks : nullptr, p.lambda,
-                             &w.scal->xmax_key, c->stream),
-                "gemm");
+      FR_TRY(fp64_gradient(c, n, K0 != nullptr, p.lambda, &w.scal->xmax_key));
       FR_CUDA(cudaEventRecord(c->evp[1], c->stream), "event");
       if (p.projection == FRAM_PROJ_EXACT) {
         // Step 6 variant: the exact FRA solution (T is free after the GEMMs).
@@ -523,6 +617,17 @@ fram_status fram_solve(fram_ctx* c, int n, const double* A, const double* B, con
   return solve_one(c, n, A, B, K, p, X_out, perm_out, info);
 }
 
+fram_status fram_set_sparse_density(fram_ctx* c, double max_density) {
+  if (!c) return FRAM_ERR_INVALID;
+  if (!(max_density >= 0.0 && max_density <= 1.0)) {
+    set_err(c, "fram_set_sparse_density: the fraction must lie in [0, 1]");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->sparse_density = max_density;
+  return FRAM_OK;
+}
+
 fram_status fram_node_affinity(fram_ctx* c, int n, int d, const double* F, const double* Ft,
                                double* K) {
   if (!c) return FRAM_ERR_INVALID;
@@ -555,9 +660,8 @@ fram_status fram_gradient(fram_ctx* c, int n, const double* A, const double* Nm,
   FR_LAUNCH(launch_scale(B, n, 1.0, false, w.Bs, ld, c->stream), "copy");
   FR_LAUNCH(launch_scale(Nm, n, 1.0, false, w.N, ld, c->stream), "copy");
   if (K) FR_LAUNCH(launch_scale(K, n, 1.0, false, w.Ks, ld, c->stream), "copy");
-  FR_LAUNCH(launch_dgemm(w.As, w.N, w.T, ld, n, nullptr, 0.0, nullptr, c->stream), "gemm");
-  FR_LAUNCH(launch_dgemm(w.T, w.Bs, w.X, ld, n, K ? w.Ks : nullptr, lambda, nullptr, c->stream),
-            "gemm");
+  FR_TRY(prepare_sparse(c, n));
+  FR_TRY(fp64_gradient(c, n, K != nullptr, lambda, nullptr));
   FR_CUDA(cudaMemcpy2DAsync(X, (size_t)n * sizeof(double), w.X, (size_t)ld * sizeof(double),
                             (size_t)n * sizeof(double), n, cudaMemcpyDeviceToDevice, c->stream),
           "copy X");

@@ -41,6 +41,14 @@ struct Workspace {
   DevScalars* hscal = nullptr;      // pinned host mirror
   void* mixed = nullptr;            // low-precision shadows (mixed paths)
   int mixed_cap_n = 0;
+  // Sparse gradient (FP64 path): CSR of A_s and of B_s^T, grown on demand.
+  int* sp_cnt = nullptr;            // [n] row counts
+  int* sp_rowptr[2] = {nullptr, nullptr};
+  int* sp_col[2] = {nullptr, nullptr};
+  double* sp_val[2] = {nullptr, nullptr};
+  int sp_cap_n = 0;
+  size_t sp_cap_nnz[2] = {0, 0};
+  bool sp_on[2] = {false, false};   // this solve uses CSR for A / for B
   void release();
   static size_t bytes_for(int n, int num_sms);
 };
@@ -58,6 +66,7 @@ struct fram_ctx {
   std::string last_error;
   std::atomic<uint64_t> launches{0};
   uint64_t wait_limit_ns = fram::kWaitLimitNs;
+  double sparse_density = 0.2;  // FP64 gradient uses CSR up to this fraction of nonzeros
   std::mutex mu;        // serialises the synchronous entry points
   std::mutex serve_mu;  // guards creation of the serving scheduler
   fram::Workspace ws;
@@ -84,6 +93,8 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
 
 // Mixed-precision outer loop (fram_mixed.cu).
 size_t mixed_bytes_for(int n);
+fram_status prepare_sparse(fram_ctx* c, int n);
+fram_status fp64_gradient(fram_ctx* c, int n, bool withK, double lam, unsigned long long* cmax);
 fram_status solve_mixed_loop(fram_ctx* c, int n, bool has_K, const fram_params& p,
                              fram_info* inf);
 fram_status mixed_gradient(fram_ctx* c, int n, bool has_K, double lam, int kind, float** X32);

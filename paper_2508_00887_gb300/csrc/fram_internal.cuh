@@ -204,6 +204,15 @@ int launch_scale(const double* src, int n, double inv, bool divide, double* dst,
 int launch_fill_assignment(double* N, int n, int ld, double value, cudaStream_t s);
 int launch_dgemm(const double* A, const double* B, double* C, int ld, int n, const double* K,
                  double lam, unsigned long long* cmax_bits, cudaStream_t s);
+// Sparse-graph gradient (FP64 path): CSR build and products.
+int launch_csr_count(const double* M, int ld, int n, int* rowcnt, cudaStream_t s);
+int launch_csr_scan(const int* rowcnt, int n, int* rowptr, cudaStream_t s);
+int launch_csr_fill(const double* M, int ld, int n, const int* rowptr, int* col, double* val,
+                    cudaStream_t s);
+int launch_spmm(const int* rowptr, const int* col, const double* val, int n, const double* D,
+                int ld, double* C, cudaStream_t s);
+int launch_transpose(const double* Src, double* Dst, int ld, int n, const double* Kmat,
+                     double lam, unsigned long long* cmax, cudaStream_t s);
 int launch_node_affinity(const double* F, const double* Ft, int n, int d, double* K,
                          cudaStream_t s);
 int launch_max(const double* X, int ldx, int n, unsigned long long* key, cudaStream_t s);
