@@ -88,8 +88,9 @@ typedef struct {
                           /* floor under delta (~1e-4 BF16, ~1e-5 TF32 at n = 1000)   */
   double stall_ratio; /* mixed paths, safeguard: also stop once delta <= stall_below */
   double stall_below; /* and delta > stall_ratio * previous delta (defaults 0.9 and  */
-                      /* 1e-2; stall_ratio = 0 disables).  The FP64 path ignores     */
-                      /* all three.                                                  */
+                      /* 1e-3, near the BF16 floor; stall_ratio = 0 disables).  The  */
+                      /* FP64 path ignores all three.  A slowly contracting delta    */
+                      /* far above the floor is progress, not a stall.               */
   int max_outer;      /* outer-iteration cap (default 100)                          */
   int max_sweeps;     /* SDSN sweep cap per call (default 200)                      */
   int max_polish;     /* mixed paths: FP64 polish sweep cap per call (default 0)    */

@@ -498,7 +498,7 @@ void fram_default_params(fram_params* p) {
   p->polish_tol = 1e-6;
   p->mixed_delta_tol = 5e-4;
   p->stall_ratio = 0.9;
-  p->stall_below = 1e-2;
+  p->stall_below = 1e-3;
   p->max_outer = 100;
   p->max_sweeps = 200;
   p->max_polish = 0;
