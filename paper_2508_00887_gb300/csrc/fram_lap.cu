@@ -23,9 +23,12 @@
 //     paths (the Hungarian method of Kuhn 1955 in the Jonker-Volgenant
 //     form).  The auction only shortens these paths; the result is exact
 //     either way.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "fram_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fram {
 
@@ -62,6 +65,7 @@ struct LapWs {
   unsigned long long* key;   // [n] auction: (quantised price << 20) | owner row;
                              //     completion label keys when they do not fit on chip
   unsigned long long* tkey;  // [n] completion test keys when they do not fit on chip
+  double* wmat;              // [n] W[colrow[j]][j] when it does not fit on chip
   LapCtl* ctl;
 };
 
@@ -84,6 +88,8 @@ __host__ __device__ inline LapWs carve(void* base, int n) {
   w.key = reinterpret_cast<unsigned long long*>(p);
   p += db;
   w.tkey = reinterpret_cast<unsigned long long*>(p);
+  p += db;
+  w.wmat = reinterpret_cast<double*>(p);
   p += db;
   w.ctl = reinterpret_cast<LapCtl*>(p);
   return w;
@@ -340,7 +346,7 @@ __global__ void lap_duals_kernel(const double* __restrict__ W, int ldw, int n, L
 constexpr size_t kSolveSmemCap = 225 * 1024;
 
 __host__ __device__ inline size_t solve_smem_bytes(int n) {
-  return al256((size_t)n * 8) * 3 + al256((size_t)n * 4);
+  return al256((size_t)n * 8) * 4 + al256((size_t)n * 4);
 }
 
 // Order-preserving map of a double onto uint64 with integer operations only
@@ -430,7 +436,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
   __shared__ int s_aug;
   const int tid = threadIdx.x;
   unsigned long long *dkey, *tkey;
-  double* v;
+  double *v, *wmat;
   int* colrow;
   if (use_smem) {
     unsigned char* p = lap_sm;
@@ -439,6 +445,8 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
     tkey = reinterpret_cast<unsigned long long*>(p);
     p += al256((size_t)n * 8);
     v = reinterpret_cast<double*>(p);
+    p += al256((size_t)n * 8);
+    wmat = reinterpret_cast<double*>(p);
     p += al256((size_t)n * 8);
     colrow = reinterpret_cast<int*>(p);
     for (int j = tid; j < n; j += kLapThreads) {
@@ -449,7 +457,13 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
     dkey = w.key;
     tkey = w.tkey;
     v = w.v;
+    wmat = w.wmat;
     colrow = w.colrow;
+  }
+  // W of each column's assigned row (what h needs), kept in step with colrow.
+  for (int j = tid; j < n; j += kLapThreads) {
+    const int r = colrow[j];
+    wmat[j] = r >= 0 ? W[(size_t)r * ldw + j] : 0.0;
   }
   int* pred = w.way;
   if (tid == 0) {
@@ -515,7 +529,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
           if (j < n) wv[u] = rowi[j];
         }
       }
-      if (tid == 0) s_h = -(rowi[j1] + v[j1]) - mu;
+      if (tid == 0) s_h = -(wmat[j1] + v[j1]) - mu;
       __syncthreads();
       const double h = s_h;
       best = kVisited;
@@ -576,6 +590,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
         const int r = pred[j];
         const int prev = w.rowcol[r];
         colrow[j] = r;
+        wmat[j] = W[(size_t)r * ldw + j];
         w.rowcol[r] = j;
         if (r == f) break;
         j = prev;
@@ -590,6 +605,253 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
     const int j = w.rowcol[i];
     perm[i] = j;
     val += W[(size_t)i * ldw + j];
+  }
+  val = warp_sum(val);
+  __shared__ double rsum[kLapThreads / 32];
+  const int lane = tid & 31, warp = tid >> 5;
+  if (lane == 0) rsum[warp] = val;
+  __syncthreads();
+  if (warp == 0) {
+    double t = rsum[lane];
+    t = warp_sum(t);
+    if (lane == 0) {
+      st->value = t;
+      st->augmented = s_aug;
+    }
+  }
+}
+
+// The same completion spread over a cluster of kLapCluster CTAs: CTA r of
+// the cluster owns the columns [r S, (r+1) S) and keeps their labels, test
+// keys, potentials and colrow in its own shared memory.  Each Dijkstra step
+// every CTA relaxes its columns and publishes its best (key, index) with the
+// row that column leads to and its potential; after one cluster barrier
+// every CTA reads the kLapCluster slots through distributed shared memory
+// and takes the same winner by the same integer comparison, so every
+// branch, return and barrier below is taken by all CTAs alike.  The choices
+// are those of lap_solve_kernel, so the results are bit-identical.
+constexpr int kLapCluster = 8;
+
+struct CandSlot {
+  unsigned long long key;
+  int k;       // argmin tie key of the candidate (j, or j + n if assigned)
+  int i;       // colrow of the candidate column
+  double vj;   // its potential
+  double wm;   // W[i][j] of the candidate
+};
+
+__global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
+    const double* __restrict__ W, int ldw, int n, LapWs w, int pass, long long budget,
+    int32_t* __restrict__ perm, LapStats* st) {
+  if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;  // uniform (earlier kernel)
+  cg::cluster_group cl = cg::this_cluster();
+  const int cr = (int)cl.block_rank();
+  const int S = (n + kLapCluster - 1) / kLapCluster;
+  const int jb = min(n, cr * S), ns = min(n, jb + S) - jb;
+  extern __shared__ __align__(16) unsigned char lap_sm[];
+  unsigned long long* dkey = reinterpret_cast<unsigned long long*>(lap_sm);
+  unsigned long long* tkey = dkey + S;
+  double* v = reinterpret_cast<double*>(tkey + S);
+  double* wmat = v + S;  // W[colrow[j]][j], kept in step with colrow
+  int* colrow = reinterpret_cast<int*>(wmat + S);
+  __shared__ CandSlot slot[2];
+  __shared__ CandSlot s_win;
+  __shared__ unsigned long long rk[kLapThreads / 32];
+  __shared__ int rkk[kLapThreads / 32];
+  __shared__ unsigned long long s_key;
+  __shared__ int s_k;
+  __shared__ double s_h;
+  __shared__ int s_aug;
+  const int tid = threadIdx.x;
+  int* pred = w.way;
+  for (int jl = tid; jl < ns; jl += kLapThreads) {
+    v[jl] = w.v[jb + jl];
+    const int r = w.colrow[jb + jl];
+    colrow[jl] = r;
+    wmat[jl] = r >= 0 ? W[(size_t)r * ldw + jb + jl] : 0.0;
+  }
+  if (tid == 0) {
+    s_aug = 0;
+    if (cr == 0) {
+      st->status = 0;
+      st->auction_phases = pass == 1 && auction_on(w.ctl) ? w.ctl->phases : -1;
+    }
+  }
+  int par = 0;
+  // This CTA's best candidate into its slot, then the cluster-wide winner
+  // and, from the winner's slot, h = c_i,j1 - v_j1 - mu of the next step.
+  auto exchange = [&](unsigned long long best, int bk, unsigned long long& key, int& k, int& i,
+                      double& h) {
+    block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+    if (tid == 0) {
+      CandSlot c{s_key, s_k, -2, 0.0, 0.0};
+      if (s_key != kVisited && s_k < 2 * n) {
+        const int jl = (s_k >= n ? s_k - n : s_k) - jb;
+        c.i = colrow[jl];
+        c.vj = v[jl];
+        c.wm = wmat[jl];
+      }
+      slot[par] = c;
+    }
+    cl.sync();
+    // Lane r of warp 0 reads CTA r's slot; a shuffle reduction picks the
+    // winner, which the rest of the CTA reads from local shared memory.
+    if (tid < 32) {
+      CandSlot c{kVisited, 0x7fffffff, -2, 0.0, 0.0};
+      if (tid < kLapCluster) c = *cl.map_shared_rank(&slot[par], tid);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, c.key, o);
+        const int okk = __shfl_xor_sync(0xffffffffu, c.k, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, c.i, o);
+        const double ov = __shfl_xor_sync(0xffffffffu, c.vj, o);
+        const double ow = __shfl_xor_sync(0xffffffffu, c.wm, o);
+        if (ok < c.key || (ok == c.key && okk < c.k)) {
+          c.key = ok;
+          c.k = okk;
+          c.i = oi;
+          c.vj = ov;
+          c.wm = ow;
+        }
+      }
+      if (tid == 0) {
+        s_win = c;
+        s_h = -(c.wm + c.vj) - okey_value(c.key);
+      }
+    }
+    __syncthreads();
+    key = s_win.key;
+    k = s_win.k;
+    i = s_win.i;
+    h = s_h;
+    par ^= 1;
+  };
+  cl.sync();
+
+  long long total = 0;
+  for (int f = 0; f < n; ++f) {
+    if (w.rowcol[f] != -1) continue;  // uniform: written before the last cluster barrier
+    const double* rowf = W + (size_t)f * ldw;
+    unsigned long long best = kVisited;
+    int bk = 0x7fffffff;
+    for (int jl = tid; jl < ns; jl += kLapThreads) {
+      const int j = jb + jl;
+      const double x = rowf[j];
+      const unsigned long long dk = okey(-(x + v[jl]));
+      dkey[jl] = dk;
+      tkey[jl] = okey(x);
+      pred[j] = f;
+      const int kk = colrow[jl] == -1 ? j : j + n;
+      if (dk < best || (dk == best && kk < bk)) {
+        best = dk;
+        bk = kk;
+      }
+    }
+    unsigned long long key;
+    int k, i;
+    double h;
+    exchange(best, bk, key, k, i, h);
+    double mu = okey_value(key);
+    int steps = 0, j1;
+    while (true) {
+      if (k < 0 || k >= 2 * n || key == kVisited) {  // no finite label left (all CTAs)
+        if (cr == 0 && tid == 0) st->status = 1;
+        cl.sync();  // no CTA leaves while another may still read its slot
+        return;
+      }
+      j1 = k >= n ? k - n : k;
+      if (j1 >= jb && j1 < jb + ns && (j1 - jb) % kLapThreads == tid) {
+        tkey[j1 - jb] = (unsigned long long)__double_as_longlong(mu);
+        dkey[j1 - jb] = kVisited;
+      }
+      if (i == -1) break;  // j1 is free: augment
+      const double* rowi = W + (size_t)i * ldw;
+      double wv[kSolveUnroll];
+      const bool pre = ns <= kSolveUnroll * kLapThreads;
+      if (pre) {
+#pragma unroll
+        for (int u = 0; u < kSolveUnroll; ++u) {
+          const int jl = tid + u * kLapThreads;
+          if (jl < ns) wv[u] = rowi[jb + jl];
+        }
+      }
+      best = kVisited;
+      bk = 0x7fffffff;
+      for (int base = tid; base < ns; base += kSolveUnroll * kLapThreads) {
+        if (!pre || base != tid) {
+#pragma unroll
+          for (int u = 0; u < kSolveUnroll; ++u) {
+            const int jl = base + u * kLapThreads;
+            if (jl < ns) wv[u] = rowi[jb + jl];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveUnroll; ++u) {
+          const int jl = base + u * kLapThreads;
+          if (jl >= ns) continue;
+          unsigned long long dk = dkey[jl];
+          if (dk == kVisited) continue;
+          const double x = wv[u] + h;
+          const unsigned long long xk = okey(x);
+          if (xk > tkey[jl]) {
+            tkey[jl] = xk;
+            const unsigned long long nk = okey(-(x + v[jl]));
+            if (nk < dk) {
+              dk = nk;
+              dkey[jl] = nk;
+              pred[jb + jl] = i;
+            }
+          }
+          const int kk = colrow[jl] == -1 ? jb + jl : jb + jl + n;
+          if (dk < best || (dk == best && kk < bk)) {
+            best = dk;
+            bk = kk;
+          }
+        }
+      }
+      exchange(best, bk, key, k, i, h);
+      mu = okey_value(key);
+      ++total;
+      if (++steps > n) {
+        if (cr == 0 && tid == 0) st->status = 1;
+        cl.sync();
+        return;
+      }
+      if (budget > 0 && total > budget) {
+        if (cr == 0 && tid == 0) atomicExch(&w.ctl->need_auction, 1);
+        cl.sync();
+        return;
+      }
+    }
+    // Potentials of the popped columns, then (CTA 0) flip the path.
+    for (int jl = tid; jl < ns; jl += kLapThreads)
+      if (dkey[jl] == kVisited) v[jl] += __longlong_as_double((long long)tkey[jl]) - mu;
+    cl.sync();  // every CTA's pred writes and potentials are done
+    if (cr == 0 && tid == 0) {
+      int j = j1;
+      while (true) {
+        const int r = pred[j];
+        const int prev = w.rowcol[r];
+        const int owner = j / S;
+        int* rc = cl.map_shared_rank(colrow, owner);
+        double* rw = cl.map_shared_rank(wmat, owner);
+        rc[j - owner * S] = r;
+        rw[j - owner * S] = W[(size_t)r * ldw + j];
+        w.rowcol[r] = j;
+        if (r == f) break;
+        j = prev;
+      }
+      ++s_aug;
+    }
+    cl.sync();
+  }
+
+  if (cr != 0) return;
+  double val = 0.0;
+  for (int r = tid; r < n; r += kLapThreads) {
+    const int j = w.rowcol[r];
+    perm[r] = j;
+    val += W[(size_t)r * ldw + j];
   }
   val = warp_sum(val);
   __shared__ double rsum[kLapThreads / 32];
@@ -636,8 +898,42 @@ int launch_auction(const double* W, int ldw, int n, LapWs w, int num_sms, uint64
 
 }  // namespace
 
+namespace {
+
+// Can a cluster of kLapCluster CTAs with `smem` bytes each be resident?
+bool cluster_ok(size_t smem) {
+  static size_t set_for = 0;
+  if (set_for < smem) {
+    if (cudaFuncSetAttribute(lap_solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSolveSmemCap) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    set_for = kSolveSmemCap;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kLapCluster);
+  cfg.blockDim = dim3(kLapThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kLapCluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, lap_solve_cluster_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
+
+}  // namespace
+
 size_t lap_workspace_bytes(int n) {
-  return 6 * al256((size_t)n * sizeof(int)) + 5 * al256((size_t)n * sizeof(double)) +
+  return 6 * al256((size_t)n * sizeof(int)) + 6 * al256((size_t)n * sizeof(double)) +
          al256(sizeof(LapCtl));
 }
 
@@ -662,19 +958,44 @@ int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, voi
     attr_set = true;
   }
   const size_t dsm = use_smem ? sm : 0;
+  // The cluster completion for large n (its column state fits on chip up to
+  // n = 8 x 7,800); the one-CTA kernel below that.
+  const int S = (n + kLapCluster - 1) / kLapCluster;
+  const size_t csm = (size_t)S * (4 * sizeof(double) + sizeof(int));
+  const bool use_cluster = n >= 1024 && csm <= kSolveSmemCap && cluster_ok(csm);
+  auto solve = [&](int pass, long long bud) -> bool {
+    if (use_cluster) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(kLapCluster);
+      cfg.blockDim = dim3(kLapThreads);
+      cfg.dynamicSmemBytes = csm;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kLapCluster;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, lap_solve_cluster_kernel, W, ldw, n, w, pass, bud, perm,
+                                st) == cudaSuccess;
+    }
+    lap_solve_kernel<<<1, kLapThreads, dsm, s>>>(W, ldw, n, w, pass, bud, use_smem, perm, st);
+    return cudaPeekAtLastError() == cudaSuccess;
+  };
   lap_init_kernel<<<blocks, 256, 0, s>>>(w, n);
   lap_rowmax_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w);
   lap_conflicts_kernel<<<blocks, 256, 0, s>>>(w, n);
   lap_candidates_kernel<<<blocks, 256, 0, s>>>(w, n, 0);
   lap_duals_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w, 0);
-  lap_solve_kernel<<<1, kLapThreads, dsm, s>>>(W, ldw, n, w, 0, budget, use_smem, perm, st);
+  if (!solve(0, budget)) return -1;
   int launches = 6;
   if (can_auction) {
     // Each of these returns at once unless the first completion ran out.
     if (launch_auction(W, ldw, n, w, num_sms, limit_ns, s) < 0) return -1;
     lap_candidates_kernel<<<blocks, 256, 0, s>>>(w, n, 1);
     lap_duals_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w, 1);
-    lap_solve_kernel<<<1, kLapThreads, dsm, s>>>(W, ldw, n, w, 1, 0, use_smem, perm, st);
+    if (!solve(1, 0)) return -1;
     launches += 4;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
