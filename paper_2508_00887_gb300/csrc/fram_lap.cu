@@ -364,6 +364,7 @@ constexpr unsigned long long kVisited = ~0ull;  // label key of a popped column
 
 // Block-wide argmin over (key, k) pairs, lexicographic, integer compares.
 // The result is in *s_key / *s_k for every thread after the call.
+template <int NT>
 __device__ __forceinline__ void block_argmin_key(unsigned long long key, int k,
                                                  unsigned long long* rk, int* rkk,
                                                  unsigned long long* s_key, int* s_k) {
@@ -383,8 +384,8 @@ __device__ __forceinline__ void block_argmin_key(unsigned long long key, int k,
   }
   __syncthreads();
   if (warp == 0) {
-    key = lane < (kLapThreads / 32) ? rk[lane] : kVisited;
-    k = lane < (kLapThreads / 32) ? rkk[lane] : 0x7fffffff;
+    key = lane < (NT / 32) ? rk[lane] : kVisited;
+    k = lane < (NT / 32) ? rkk[lane] : 0x7fffffff;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
         }
       }
     }
-    block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+    block_argmin_key<kLapThreads>(best, bk, rk, rkk, &s_key, &s_k);
     double mu = okey_value(s_key);
     int key = s_k;
     int steps = 0;
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
           }
         }
       }
-      block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+      block_argmin_key<kLapThreads>(best, bk, rk, rkk, &s_key, &s_k);
       mu = okey_value(s_key);
       key = s_k;
       ++total;
@@ -631,6 +632,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
 // branch, return and barrier below is taken by all CTAs alike.  The choices
 // are those of lap_solve_kernel, so the results are bit-identical.
 constexpr int kLapCluster = 8;
+constexpr int kClusterThreads = 256;  // per CTA: a cheaper CTA and cluster barrier
 
 struct CandSlot {
   unsigned long long key;
@@ -640,7 +642,7 @@ struct CandSlot {
   double wm;   // W[i][j] of the candidate
 };
 
-__global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
+__global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     const double* __restrict__ W, int ldw, int n, LapWs w, int pass, long long budget,
     int32_t* __restrict__ perm, LapStats* st) {
   if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;  // uniform (earlier kernel)
@@ -656,15 +658,15 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
   int* colrow = reinterpret_cast<int*>(wmat + S);
   __shared__ CandSlot slot[2];
   __shared__ CandSlot s_win;
-  __shared__ unsigned long long rk[kLapThreads / 32];
-  __shared__ int rkk[kLapThreads / 32];
+  __shared__ unsigned long long rk[kClusterThreads / 32];
+  __shared__ int rkk[kClusterThreads / 32];
   __shared__ unsigned long long s_key;
   __shared__ int s_k;
   __shared__ double s_h;
   __shared__ int s_aug;
   const int tid = threadIdx.x;
   int* pred = w.way;
-  for (int jl = tid; jl < ns; jl += kLapThreads) {
+  for (int jl = tid; jl < ns; jl += kClusterThreads) {
     v[jl] = w.v[jb + jl];
     const int r = w.colrow[jb + jl];
     colrow[jl] = r;
@@ -682,7 +684,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
   // and, from the winner's slot, h = c_i,j1 - v_j1 - mu of the next step.
   auto exchange = [&](unsigned long long best, int bk, unsigned long long& key, int& k, int& i,
                       double& h) {
-    block_argmin_key(best, bk, rk, rkk, &s_key, &s_k);
+    block_argmin_key<kClusterThreads>(best, bk, rk, rkk, &s_key, &s_k);
     if (tid == 0) {
       CandSlot c{s_key, s_k, -2, 0.0, 0.0};
       if (s_key != kVisited && s_k < 2 * n) {
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
     const double* rowf = W + (size_t)f * ldw;
     unsigned long long best = kVisited;
     int bk = 0x7fffffff;
-    for (int jl = tid; jl < ns; jl += kLapThreads) {
+    for (int jl = tid; jl < ns; jl += kClusterThreads) {
       const int j = jb + jl;
       const double x = rowf[j];
       const unsigned long long dk = okey(-(x + v[jl]));
@@ -760,34 +762,34 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
         return;
       }
       j1 = k >= n ? k - n : k;
-      if (j1 >= jb && j1 < jb + ns && (j1 - jb) % kLapThreads == tid) {
+      if (j1 >= jb && j1 < jb + ns && (j1 - jb) % kClusterThreads == tid) {
         tkey[j1 - jb] = (unsigned long long)__double_as_longlong(mu);
         dkey[j1 - jb] = kVisited;
       }
       if (i == -1) break;  // j1 is free: augment
       const double* rowi = W + (size_t)i * ldw;
       double wv[kSolveUnroll];
-      const bool pre = ns <= kSolveUnroll * kLapThreads;
+      const bool pre = ns <= kSolveUnroll * kClusterThreads;
       if (pre) {
 #pragma unroll
         for (int u = 0; u < kSolveUnroll; ++u) {
-          const int jl = tid + u * kLapThreads;
+          const int jl = tid + u * kClusterThreads;
           if (jl < ns) wv[u] = rowi[jb + jl];
         }
       }
       best = kVisited;
       bk = 0x7fffffff;
-      for (int base = tid; base < ns; base += kSolveUnroll * kLapThreads) {
+      for (int base = tid; base < ns; base += kSolveUnroll * kClusterThreads) {
         if (!pre || base != tid) {
 #pragma unroll
           for (int u = 0; u < kSolveUnroll; ++u) {
-            const int jl = base + u * kLapThreads;
+            const int jl = base + u * kClusterThreads;
             if (jl < ns) wv[u] = rowi[jb + jl];
           }
         }
 #pragma unroll
         for (int u = 0; u < kSolveUnroll; ++u) {
-          const int jl = base + u * kLapThreads;
+          const int jl = base + u * kClusterThreads;
           if (jl >= ns) continue;
           unsigned long long dk = dkey[jl];
           if (dk == kVisited) continue;
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
       }
     }
     // Potentials of the popped columns, then (CTA 0) flip the path.
-    for (int jl = tid; jl < ns; jl += kLapThreads)
+    for (int jl = tid; jl < ns; jl += kClusterThreads)
       if (dkey[jl] == kVisited) v[jl] += __longlong_as_double((long long)tkey[jl]) - mu;
     cl.sync();  // every CTA's pred writes and potentials are done
     if (cr == 0 && tid == 0) {
@@ -848,18 +850,18 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_cluster_kernel(
 
   if (cr != 0) return;
   double val = 0.0;
-  for (int r = tid; r < n; r += kLapThreads) {
+  for (int r = tid; r < n; r += kClusterThreads) {
     const int j = w.rowcol[r];
     perm[r] = j;
     val += W[(size_t)r * ldw + j];
   }
   val = warp_sum(val);
-  __shared__ double rsum[kLapThreads / 32];
+  __shared__ double rsum[kClusterThreads / 32];
   const int lane = tid & 31, warp = tid >> 5;
   if (lane == 0) rsum[warp] = val;
   __syncthreads();
   if (warp == 0) {
-    double t = rsum[lane];
+    double t = lane < kClusterThreads / 32 ? rsum[lane] : 0.0;
     t = warp_sum(t);
     if (lane == 0) {
       st->value = t;
@@ -913,7 +915,7 @@ bool cluster_ok(size_t smem) {
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kLapCluster);
-  cfg.blockDim = dim3(kLapThreads);
+  cfg.blockDim = dim3(kClusterThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -967,7 +969,7 @@ int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, voi
     if (use_cluster) {
       cudaLaunchConfig_t cfg{};
       cfg.gridDim = dim3(kLapCluster);
-      cfg.blockDim = dim3(kLapThreads);
+      cfg.blockDim = dim3(kClusterThreads);
       cfg.dynamicSmemBytes = csm;
       cfg.stream = s;
       cudaLaunchAttribute at[1];
