@@ -26,8 +26,11 @@
 // shrinks, and when its size repeats the root is exact (Michelot's rule).
 // The first evaluation, f_i at the previous value, is row i's residual at
 // the current point, so the stop test costs nothing extra.  Comparisons use
-// order-preserving integer keys and each pass costs one FP64 add per
-// element (plus one per active element): FP64 is scarce on this GPU.
+// order-preserving integer keys.  FP64 is scarce on this GPU, so for n up to
+// 2048 a warp forms z_j = Y0_ij - v_j once per equation and keeps only the
+// keys of z in registers (the key is a bijection, so z comes back exactly);
+// a Newton pass then costs integer compares plus one FP64 add per active
+// element.  Larger n streams z again on every pass (one add per element).
 //
 // Over-relaxation: both steps move omega = 1.6 of the way to the solved
 // value while the row residual keeps falling, 1 otherwise; once the residual
@@ -114,14 +117,132 @@ __device__ double warp_threshold(const double* __restrict__ y, const double* v, 
   return a;
 }
 
+// warp_threshold with the keys of z held in registers: C chunks of 32 per
+// lane, n <= 32 C.  A pass over the registers also compacts the keys above
+// the current a into the warp's list (ballot and popcount, integer work
+// only); while a stays at or above the point the list was built at, the
+// next passes read only the list, so a pass costs about (active / 32) FP64
+// adds per lane instead of one per chunk.  A list that would overflow is
+// not kept and the pass sums from the registers.
+constexpr int kListCap = 256;
+
+template <int C>
+__device__ double warp_threshold_reg(const double* __restrict__ y, const double* v, int n,
+                                     bool cold, double w0, double* res,
+                                     unsigned long long* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long zk[C];
+  unsigned long long zmax = 0;  // below the key of every finite value
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int j = lane + 32 * c;
+    zk[c] = 0;
+    if (j < n) {
+      const double z = y[j] - v[j];
+      zk[c] = ordered_key(z);
+      if (cold) s += z;
+    }
+    zmax = zk[c] > zmax ? zk[c] : zmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long oz = __shfl_xor_sync(0xffffffffu, zmax, o);
+    zmax = oz > zmax ? oz : zmax;
+  }
+  double a = w0;
+  if (cold) a = (warp_sum(s) - 1.0) / n;
+  int m = -1;                   // list length (-1: no list)
+  unsigned long long lkey = 0;  // key of the a the list was built at
+  int kprev = -1;
+  for (int it = 0; it < kMaxNewton; ++it) {
+    const unsigned long long ak = ordered_key(a);
+    double S = 0.0;
+    int k = 0;
+    if (m < 0 || ak < lkey) {
+      // Pass over the registers, compacting {z > a} into the list.
+      __syncwarp();  // every lane is done reading the old list
+      int base = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const bool act = zk[c] > ak;
+        const unsigned msk = __ballot_sync(0xffffffffu, act);
+        const int pos = base + __popc(msk & lt);
+        if (act && pos < kListCap) list[pos] = zk[c];
+        base += __popc(msk);
+      }
+      __syncwarp();
+      lkey = ak;
+      m = base <= kListCap ? base : -1;
+      if (m < 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if (zk[c] > ak) {
+            S += from_ordered_key(zk[c]);
+            ++k;
+          }
+        }
+      } else {
+        for (int t = lane; t < m; t += 32) {
+          S += from_ordered_key(list[t]);
+          ++k;
+        }
+      }
+    } else {
+      for (int t = lane; t < m; t += 32) {
+        const unsigned long long q = list[t];
+        if (q > ak) {
+          S += from_ordered_key(q);
+          ++k;
+        }
+      }
+    }
+    S = warp_sum(S);
+    k = __reduce_add_sync(0xffffffffu, k);
+    if (it == 0 && !cold) *res = fabs(S - k * a - 1.0);
+    if (k == kprev) break;
+    kprev = k;
+    if (k == 0) {
+      a = from_ordered_key(zmax) - 1.0;
+      kprev = -1;
+      continue;
+    }
+    a = (S - 1.0) / k;
+  }
+  return a;
+}
+
+// C = 0: stream z on every pass; C > 0: warp_threshold_reg<C>.
+template <int C>
+__device__ __forceinline__ double threshold(const double* __restrict__ y, const double* v, int n,
+                                            bool cold, double w0, double* res,
+                                            unsigned long long* list) {
+  if constexpr (C == 0)
+    return warp_threshold(y, v, n, cold, w0, res);
+  else
+    return warp_threshold_reg<C>(y, v, n, cold, w0, res, list);
+}
+
+// Dynamic shared memory: a and b (n doubles each), then with C > 0 one
+// key list per warp.
+template <int C>
+size_t fra_smem_bytes(int n) {
+  return 2 * (size_t)n * sizeof(double) +
+         (C > 0 ? (size_t)kFraWarps * kListCap * sizeof(unsigned long long) : 0);
+}
+
+template <int C>
 __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
-  extern __shared__ double fra_sm[];  // a_s[n], b_s[n]
+  extern __shared__ double fra_sm[];  // a_s[n], b_s[n], lists
   __shared__ double s_res[kFraWarps];
   __shared__ int s_flag;
   const int n = p.n;
   double* a_s = fra_sm;
   double* b_s = fra_sm + n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long* list =
+      reinterpret_cast<unsigned long long*>(fra_sm + 2 * (size_t)n) + (size_t)warp * kListCap;
   const int G = gridDim.x, blk = blockIdx.x;
   const int R = (n + G - 1) / G;
   const int i0 = min(n, blk * R), i1 = min(n, i0 + R);
@@ -165,7 +286,7 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
     for (int i = i0 + warp; i < i1; i += kFraWarps) {
       double r = 0.0;
       const double w0 = k > 0 ? a_cur[i] : 0.0;
-      const double t = warp_threshold(p.Y + (size_t)i * p.ldy, b_s, n, k == 0, w0, &r);
+      const double t = threshold<C>(p.Y + (size_t)i * p.ldy, b_s, n, k == 0, w0, &r, list);
       if (lane == 0) a_new[i] = k > 0 ? w0 + omega * (t - w0) : t;
       lres = fmax(lres, r);
     }
@@ -196,7 +317,7 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
     for (int j = i0 + warp; j < i1; j += kFraWarps) {
       double r = 0.0;
       const double w0 = b_s[j];
-      const double t = warp_threshold(p.Yt + (size_t)j * p.ldt, a_s, n, k == 0, w0, &r);
+      const double t = threshold<C>(p.Yt + (size_t)j * p.ldt, a_s, n, k == 0, w0, &r, list);
       if (lane == 0) p.bv[j] = k > 0 ? w0 + w_col * (t - w0) : t;
     }
     col_plain = k == 0 || w_col == 1.0;
@@ -227,30 +348,44 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
 
 size_t fra_workspace_elems(int n, int num_sms) { return 3 * (size_t)n + 2 * (size_t)num_sms; }
 
-int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned long long* xmax_key,
-               double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
-               SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)n * sizeof(double);
-  if (smem > 200 * 1024) return -1;  // the two multiplier vectors live in shared memory
-  static int per_sm = 0;
-  static size_t attr_smem = 0;
-  if (attr_smem < smem) {
-    if (cudaFuncSetAttribute(fra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
+namespace {
+
+template <int C>
+int launch_fra_c(const FraK& k, int n, int num_sms, cudaStream_t s) {
+  const size_t smem = fra_smem_bytes<C>(n);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(fra_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             216 * 1024) != cudaSuccess)
       return -1;
-    attr_smem = 200 * 1024;
+    attr = true;
   }
+  // Occupancy depends on smem (n); query it for each launch size.
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fra_kernel, kFraThreads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fra_kernel<C>, kFraThreads, smem) !=
           cudaSuccess ||
       occ < 1)
     return -1;
-  per_sm = occ;
   // About one warp per row of the owned block; no more CTAs than rows.
-  int grid = per_sm * num_sms;
+  int grid = occ * num_sms;
   const int want = (n + kFraWarps - 1) / kFraWarps;
   if (grid > want) grid = want > num_sms ? want : (n < num_sms ? n : num_sms);
   if (grid < 1) grid = 1;
+  if (cudaMemsetAsync(k.bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
+  FraK kk = k;
+  void* args[] = {&kk};
+  if (cudaLaunchCooperativeKernel((const void*)fra_kernel<C>, dim3(grid), dim3(kFraThreads), args,
+                                  smem, s) != cudaSuccess)
+    return -1;
+  return 1;
+}
+
+}  // namespace
+
+int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned long long* xmax_key,
+               double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
+               SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s) {
+  if (2 * (size_t)n * sizeof(double) > 200 * 1024) return -1;  // a and b live in shared memory
   FraK k{};
   k.n = n;
   k.Y = Y;
@@ -267,12 +402,11 @@ int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned lo
   k.bar = bar;
   k.stats = stats;
   k.limit_ns = limit_ns;
-  if (cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
-  void* args[] = {&k};
-  if (cudaLaunchCooperativeKernel((const void*)fra_kernel, dim3(grid), dim3(kFraThreads), args,
-                                  smem, s) != cudaSuccess)
-    return -1;
-  return 1;
+  if (n <= 256) return launch_fra_c<8>(k, n, num_sms, s);
+  if (n <= 512) return launch_fra_c<16>(k, n, num_sms, s);
+  if (n <= 1024) return launch_fra_c<32>(k, n, num_sms, s);
+  if (n <= 2048) return launch_fra_c<64>(k, n, num_sms, s);
+  return launch_fra_c<0>(k, n, num_sms, s);
 }
 
 }  // namespace fram

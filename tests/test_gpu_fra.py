@@ -54,6 +54,26 @@ def test_fra_exact_matches_oracle(torch_cuda, ctx, n, theta, seed):
     assert np.max(np.abs(Dg - ref.D)) <= 1e-8
 
 
+@pytest.mark.parametrize("n", [1500, 2100])
+def test_fra_exact_wide_rows(torch_cuda, ctx, n):
+    # n = 1500 keeps each equation's keys in registers (64 per lane); n = 2100
+    # is past that and streams Y0 on every Newton pass.  Random X: the
+    # oracle finishes these sizes in seconds.
+    torch = torch_cuda
+    X = np.random.default_rng(n).random((n, n))
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    tol = 1e-11
+    _, sweeps, res = fr.fram_fra_exact(ctx, n, torch.from_numpy(X).cuda(), D, 10.0, tol=tol)
+    Dg = D.cpu().numpy()
+    assert res <= tol and sweeps >= 1
+    assert np.all(Dg >= 0)
+    assert np.max(np.abs(Dg.sum(1) - 1)) <= 2 * tol
+    assert np.max(np.abs(Dg.sum(0) - 1)) <= 1e-12 * n / 100
+    ref = o.fra_exact(X, 10.0, tol=tol, omega=1.6)
+    assert ref.converged
+    assert np.max(np.abs(Dg - ref.D)) <= 1e-8
+
+
 def test_fra_exact_in_place_and_degenerate(torch_cuda, ctx):
     torch = torch_cuda
     n = 50
