@@ -625,21 +625,26 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
 // The same completion spread over a cluster of kLapCluster CTAs: CTA r of
 // the cluster owns the columns [r S, (r+1) S) and keeps their labels, test
 // keys, potentials and colrow in its own shared memory.  Each Dijkstra step
-// every CTA relaxes its columns and publishes its best (key, index) with the
-// row that column leads to and its potential; after one cluster barrier
-// every CTA reads the kLapCluster slots through distributed shared memory
-// and takes the same winner by the same integer comparison, so every
-// branch, return and barrier below is taken by all CTAs alike.  The choices
-// are those of lap_solve_kernel, so the results are bit-identical.
+// every warp relaxes its columns, takes its best (key, index) by shuffles
+// and writes it, with the row that column leads to and the next step's h,
+// into its slot in its own CTA.  After one cluster barrier warp 0 of every
+// CTA reads all kLapCluster x 8 slots through distributed shared memory (two
+// per lane) and reduces them to the same winner by the same integer
+// comparison, so every branch, return and barrier below is taken by all
+// CTAs alike.  The slots are double-buffered by step parity: a slot is
+// written again only two cluster barriers after the last remote read of it.
+// The choices are those of lap_solve_kernel, so the results are
+// bit-identical.
 constexpr int kLapCluster = 8;
 constexpr int kClusterThreads = 256;  // per CTA: a cheaper CTA and cluster barrier
+constexpr int kClusterWarps = kClusterThreads / 32;
+static_assert(kLapCluster * kClusterWarps == 64, "warp 0 reads two slots per lane");
 
 struct CandSlot {
   unsigned long long key;
-  int k;       // argmin tie key of the candidate (j, or j + n if assigned)
-  int i;       // colrow of the candidate column
-  double vj;   // its potential
-  double wm;   // W[i][j] of the candidate
+  int k;     // argmin tie key of the candidate (j, or j + n if assigned)
+  int i;     // colrow of the candidate column
+  double h;  // -(W[i][j] + v_j) - label of the candidate: the next step's h
 };
 
 __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
@@ -656,15 +661,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
   double* v = reinterpret_cast<double*>(tkey + S);
   double* wmat = v + S;  // W[colrow[j]][j], kept in step with colrow
   int* colrow = reinterpret_cast<int*>(wmat + S);
-  __shared__ CandSlot slot[2];
+  __shared__ CandSlot slots[2][kClusterWarps];
   __shared__ CandSlot s_win;
-  __shared__ unsigned long long rk[kClusterThreads / 32];
-  __shared__ int rkk[kClusterThreads / 32];
-  __shared__ unsigned long long s_key;
-  __shared__ int s_k;
-  __shared__ double s_h;
   __shared__ int s_aug;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int* pred = w.way;
   for (int jl = tid; jl < ns; jl += kClusterThreads) {
     v[jl] = w.v[jb + jl];
@@ -680,52 +680,55 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     }
   }
   int par = 0;
-  // This CTA's best candidate into its slot, then the cluster-wide winner
-  // and, from the winner's slot, h = c_i,j1 - v_j1 - mu of the next step.
+  // This warp's best candidate into its slot, then (warp 0 of each CTA) the
+  // cluster-wide winner over all slots, broadcast through s_win.
   auto exchange = [&](unsigned long long best, int bk, unsigned long long& key, int& k, int& i,
                       double& h) {
-    block_argmin_key<kClusterThreads>(best, bk, rk, rkk, &s_key, &s_k);
-    if (tid == 0) {
-      CandSlot c{s_key, s_k, -2, 0.0, 0.0};
-      if (s_key != kVisited && s_k < 2 * n) {
-        const int jl = (s_k >= n ? s_k - n : s_k) - jb;
-        c.i = colrow[jl];
-        c.vj = v[jl];
-        c.wm = wmat[jl];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+      const int ok2 = __shfl_xor_sync(0xffffffffu, bk, o);
+      if (ok < best || (ok == best && ok2 < bk)) {
+        best = ok;
+        bk = ok2;
       }
-      slot[par] = c;
+    }
+    if (lane == 0) {
+      CandSlot c{best, bk, -2, 0.0};
+      if (best != kVisited && bk < 2 * n) {  // a column of this warp: stable during the step
+        const int jl = (bk >= n ? bk - n : bk) - jb;
+        c.i = colrow[jl];
+        c.h = -(wmat[jl] + v[jl]) - okey_value(best);
+      }
+      slots[par][warp] = c;
     }
     cl.sync();
-    // Lane r of warp 0 reads CTA r's slot; a shuffle reduction picks the
-    // winner, which the rest of the CTA reads from local shared memory.
-    if (tid < 32) {
-      CandSlot c{kVisited, 0x7fffffff, -2, 0.0, 0.0};
-      if (tid < kLapCluster) c = *cl.map_shared_rank(&slot[par], tid);
+    if (warp == 0) {
+      // Lane l: slot l % 8 of CTAs l / 8 and l / 8 + 4.
+      const CandSlot c0 = *cl.map_shared_rank(&slots[par][lane & 7], lane >> 3);
+      const CandSlot c1 = *cl.map_shared_rank(&slots[par][lane & 7], (lane >> 3) + 4);
+      CandSlot c = c0;
+      if (c1.key < c.key || (c1.key == c.key && c1.k < c.k)) c = c1;
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
+      for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ok = __shfl_xor_sync(0xffffffffu, c.key, o);
-        const int okk = __shfl_xor_sync(0xffffffffu, c.k, o);
+        const int ok2 = __shfl_xor_sync(0xffffffffu, c.k, o);
         const int oi = __shfl_xor_sync(0xffffffffu, c.i, o);
-        const double ov = __shfl_xor_sync(0xffffffffu, c.vj, o);
-        const double ow = __shfl_xor_sync(0xffffffffu, c.wm, o);
-        if (ok < c.key || (ok == c.key && okk < c.k)) {
+        const double oh = __shfl_xor_sync(0xffffffffu, c.h, o);
+        if (ok < c.key || (ok == c.key && ok2 < c.k)) {
           c.key = ok;
-          c.k = okk;
+          c.k = ok2;
           c.i = oi;
-          c.vj = ov;
-          c.wm = ow;
+          c.h = oh;
         }
       }
-      if (tid == 0) {
-        s_win = c;
-        s_h = -(c.wm + c.vj) - okey_value(c.key);
-      }
+      if (lane == 0) s_win = c;
     }
     __syncthreads();
     key = s_win.key;
     k = s_win.k;
     i = s_win.i;
-    h = s_h;
+    h = s_win.h;
     par ^= 1;
   };
   cl.sync();
@@ -856,12 +859,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     val += W[(size_t)r * ldw + j];
   }
   val = warp_sum(val);
-  __shared__ double rsum[kClusterThreads / 32];
-  const int lane = tid & 31, warp = tid >> 5;
+  __shared__ double rsum[kClusterWarps];
   if (lane == 0) rsum[warp] = val;
   __syncthreads();
   if (warp == 0) {
-    double t = lane < kClusterThreads / 32 ? rsum[lane] : 0.0;
+    double t = lane < kClusterWarps ? rsum[lane] : 0.0;
     t = warp_sum(t);
     if (lane == 0) {
       st->value = t;
