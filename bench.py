@@ -231,6 +231,26 @@ def time_solves(fr, torch, ctx, n, A, B, params, steps, warmup, flush, node=None
     return ms, infos, X, P, fr.fram_kernel_launches(ctx) - launches0
 
 
+# FP32 CUDA-core peak of one GB300 for the batched kernel's ALU roofline:
+# 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock.
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def batch_roofline(ns, infos, step_s):
+    """ALU roofline of the batched kernel (one launch per call; the gather and
+    scatter kernels around it take under 0.3% of the call).  Algorithmic FP32
+    flops per pair: per outer iteration the two n^3 products (4 n^3) and the
+    update with its delta (6 n^2); per SDSN sweep 7 n^2 (row and column sums,
+    the three-term affine map of eq. 7, the gamma sum)."""
+    flops = sum(i.outer_iters * (4.0 * n ** 3 + 6.0 * n * n) + i.total_sweeps * 7.0 * n * n
+                for n, i in zip(ns, infos))
+    achieved = flops / step_s / 1e12
+    return {"kernel": "batched_kernel<float>", "bound": "alu", "achieved": achieved,
+            "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS,
+            "traffic": None, "per_launch_us": step_s * 1e6,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+
+
 def run_batch(args):
     """Batched workload: one step = one fram_solve_batched call (one persistent
     kernel launch replayed from a CUDA graph) over 4096 small pairs."""
@@ -304,6 +324,7 @@ def run_batch(args):
             "e2e": {"value": ws * len(pairs) / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(sum(2 * g.n * g.n * 8 for g in pairs)),
                     "d2h_bytes_per_step": int(sum(g.n * 4 for g in pairs))},
+            "roofline": batch_roofline(ns, infos, total_s / args.steps),
             "gpu_launches": int(launches), "clocks": clk.summary(),
         }
         if not args.no_cpu_baseline and ws == 1:
@@ -424,6 +445,11 @@ def run_serve(args):
         "solve": {"mean_accuracy": acc, "sample_size": len(sample),
                   "sample_accuracy": float(np.mean(acc_m)),
                   "sample_oracle_accuracy": float(np.mean(acc_o))},
+        # The serving rate is itself end to end: numpy host inputs go in
+        # through fram_submit and permutations come back through fram_poll.
+        "e2e": {"value": len(done) / elapsed, "unit": UNIT,
+                "h2d_bytes_per_step": float(np.mean([16.0 * d[2].n ** 2 for d in done])),
+                "d2h_bytes_per_step": float(np.mean([4.0 * d[2].n for d in done]))},
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -568,6 +594,24 @@ def run_ours(args):
     return 0
 
 
+def sdsn_traffic(n, s, sweeps_per_launch):
+    """DRAM bytes per FP32 SDSN launch (dram__bytes_read.sum +
+    dram__bytes_write.sum, one ncu capture of the current kernel), or None
+    where no capture covers the size:
+      n = 1000: 4.16 MB per launch, whatever the sweep count: the tiles stay
+        in shared memory and only X is read (capture of this workload);
+      n >= 6144 (the matrix far above L2): 7.85 bytes per element per pass,
+        measured at n = 6144 (59.16 GB over 201 passes of 6144^2), scaled to
+        n^2 (sweeps + 1) bytes."""
+    if s != 4:
+        return None
+    if n == 1000:
+        return 4.16e6
+    if n >= 6144:
+        return 7.85 * n * n * (sweeps_per_launch + 1.0)
+    return None
+
+
 def roofline(infos, n, precision, pk, src):
     """Roofline of the dominant phase, from the live per-phase device times of
     the timed steps (CUDA events on the solve's stream).
@@ -599,10 +643,11 @@ def roofline(infos, n, precision, pk, src):
             "bound": "alu" if precision == "fp64" else "tensor",
             "achieved": gemm_flops / (ms_gemm / 1e3) / 1e12 if ms_gemm else None,
             "peak": peak_t, "unit": "TFLOP/s", "peak_source": unit_peak}
+    sdsn["traffic"] = sdsn_traffic(n, s, sweeps / max(launches, 1))
+    gemm["traffic"] = None
     dom, other = (sdsn, gemm) if ms_sdsn >= ms_gemm else (gemm, sdsn)
     dom = dict(dom)
     dom["frac"] = dom["achieved"] / dom["peak"] if dom["achieved"] and dom["peak"] else None
-    dom["traffic"] = None
     dom["peak_source"] = dom.get("peak_source", f"{src} hbm_gbs")
     dom["time_share"] = {"sdsn_ms": ms_sdsn, "gemm_ms": ms_gemm,
                          "polish_ms": sum(i.ms_polish for i in infos),

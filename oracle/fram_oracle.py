@@ -9,8 +9,8 @@ library and imports nothing from the product package.
 Every function follows one passage of the paper, cited in its docstring, in
 the paper's order and notation.  Matrix products use ``numpy.matmul`` (a
 library primitive); everything else is written out.  Where the paper is
-silent, garbled or inconsistent, the reading taken is stated as "Reading
-(x)" and listed in DESIGN.md.
+silent, garbled or inconsistent, the reading taken is stated where it is
+used, as "Reading (x)".
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (closed forms, KKT solves, brute force,
