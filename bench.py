@@ -251,6 +251,48 @@ def batch_roofline(ns, infos, step_s):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
 
 
+def batch_vs_fp64(fr, ctx, stream, flush, ns, As, Bs, params, pairs, args, o):
+    """The same pairs through the FP64 batched path: its rate (same timing
+    rules: CUDA events per call, L2 flushed before each) and the mixed
+    results' distance from it (accuracy, objective, X)."""
+    import torch
+    p64 = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_FP64)
+    P64 = [torch.empty(n, dtype=torch.int32, device="cuda") for n in ns]
+    X64 = [torch.empty((n, n), dtype=torch.float64, device="cuda") for n in ns]
+    Xm = [torch.empty((n, n), dtype=torch.float64, device="cuda") for n in ns]
+    Pm = [torch.empty(n, dtype=torch.int32, device="cuda") for n in ns]
+    for _ in range(2):  # warm-up: autotune and graph capture for this signature
+        fr.fram_solve_batched(ctx, ns, As, Bs, p64, X64, P64)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, i64 = fr.fram_solve_batched(ctx, ns, As, Bs, p64, X64, P64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    _, im = fr.fram_solve_batched(ctx, ns, As, Bs, params, Xm, Pm)
+    torch.cuda.synchronize()
+    acc64 = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(P64, pairs)]
+    accm = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Pm, pairs)]
+    same = [bool(torch.equal(a, b)) for a, b in zip(Pm, P64)]
+    obj = [abs(x.objective - y.objective) / max(abs(y.objective), 1e-300) for x, y in zip(im, i64)]
+    xerr = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(Xm, X64)]
+    return {"fp64": {"value": len(ns) * steps / (sum(ms) / 1e3), "unit": UNIT,
+                     "ms_per_step": sum(ms) / steps,
+                     "mean_outer_iters": float(np.mean([i.outer_iters for i in i64])),
+                     "mean_accuracy": float(np.mean(acc64))},
+            "accuracy": {"accuracy_pp": 100.0 * (float(np.mean(accm)) - float(np.mean(acc64))),
+                         "objective_rel_err_max": float(np.max(obj)),
+                         "objective_rel_err_mean": float(np.mean(obj)),
+                         "X_rel_err_mean": float(np.mean(xerr)),
+                         "X_rel_err_max": float(np.max(xerr)),
+                         "perm_identical_frac": float(np.mean(same))}}
+
+
 def run_batch(args):
     """Batched workload: one step = one fram_solve_batched call (one persistent
     kernel launch replayed from a CUDA graph) over 4096 small pairs."""
@@ -310,6 +352,7 @@ def run_batch(args):
     if rank == 0:
         import oracle as o
         acc = float(np.mean([o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Ps, pairs)]))
+        vs64 = batch_vs_fp64(fr, ctx, stream, flush, ns, As, Bs, params, pairs, args, o)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
@@ -325,6 +368,8 @@ def run_batch(args):
                     "h2d_bytes_per_step": int(sum(2 * g.n * g.n * 8 for g in pairs)),
                     "d2h_bytes_per_step": int(sum(g.n * 4 for g in pairs))},
             "roofline": batch_roofline(ns, infos, total_s / args.steps),
+            "fp64": vs64["fp64"], "speedup_vs_fp64": value / ws / vs64["fp64"]["value"],
+            "vs_fp64_accuracy": vs64["accuracy"],
             "gpu_launches": int(launches), "clocks": clk.summary(),
         }
         if not args.no_cpu_baseline and ws == 1:
@@ -347,6 +392,40 @@ def run_batch(args):
 SERVE_DESC = ("Poisson stream, n log-uniform on [20, 2048], ER p=0.1 U(0,1) weights, planted "
               "permutation + N(0,0.05) noise, theta=10; offered load 0.7 x measured saturated rate; "
               "requests draw from a pool of pre-generated pairs")
+
+
+def serve_vs_fp64(fr, ctx, params, reqs, o):
+    """The same requests served at FP64 and at the bench precision, each set
+    submitted at once (saturated): the two rates and the distance of the
+    mixed results from the FP64 ones."""
+    p64 = fr.fram_default_params(theta=10.0, precision=fr.FRAM_PREC_FP64)
+
+    def run(p):
+        t0 = time.perf_counter()
+        tk = [fr.fram_submit(ctx, g.n, g.A, g.B, p)[1] for g in reqs]
+        out = []
+        for t, g in zip(tk, reqs):
+            P = np.empty(g.n, np.int32)
+            _, info = fr.fram_poll(ctx, t, None, P, wait_ms=-1)
+            out.append((P, info.objective))
+        return len(reqs) / (time.perf_counter() - t0), out
+
+    run(p64)  # warm-up at FP64 (kernels and slots)
+    r64, o64 = run(p64)
+    rm, om = run(params)
+    acc64 = [o.accuracy(P, g.truth) for (P, _), g in zip(o64, reqs)]
+    accm = [o.accuracy(P, g.truth) for (P, _), g in zip(om, reqs)]
+    obj = [abs(a[1] - b[1]) / max(abs(b[1]), 1e-300) for a, b in zip(om, o64)]
+    same = [bool(np.array_equal(a[0], b[0])) for a, b in zip(om, o64)]
+    return {"fp64": {"value": r64, "unit": UNIT, "requests": len(reqs),
+                     "mean_accuracy": float(np.mean(acc64)),
+                     "note": "saturated: all requests submitted at once; mixed on the same set: "
+                             f"{rm:.2f} solves/s"},
+            "speedup": rm / r64,
+            "accuracy": {"accuracy_pp": 100.0 * (float(np.mean(accm)) - float(np.mean(acc64))),
+                         "objective_rel_err_max": float(np.max(obj)),
+                         "objective_rel_err_mean": float(np.mean(obj)),
+                         "perm_identical_frac": float(np.mean(same))}}
 
 
 def run_serve(args):
@@ -428,6 +507,7 @@ def run_serve(args):
     launches = fr.fram_kernel_launches(ctx) - l0
     lat = np.array([d[0] for d in done])
     import oracle as o
+    vs64 = serve_vs_fp64(fr, ctx, params, sat_g[:args.serve_fp64], o)
     acc = float(np.mean([o.accuracy(d[1], d[2].truth) for d in done]))
     # 1% sample against the oracle (requests with n <= 400 keep the CPU bounded)
     small = [d for d in done if d[2].n <= 400]
@@ -450,6 +530,8 @@ def run_serve(args):
         "e2e": {"value": len(done) / elapsed, "unit": UNIT,
                 "h2d_bytes_per_step": float(np.mean([16.0 * d[2].n ** 2 for d in done])),
                 "d2h_bytes_per_step": float(np.mean([4.0 * d[2].n for d in done]))},
+        "fp64": vs64["fp64"], "speedup_vs_fp64": vs64["speedup"],
+        "vs_fp64_accuracy": vs64["accuracy"],
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -669,6 +751,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=2000)
     ap.add_argument("--serve-sat", type=int, default=400)
     ap.add_argument("--serve-pool", type=int, default=48)
+    ap.add_argument("--serve-fp64", type=int, default=100,
+                    help="saturation requests also served at FP64 for the comparison")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--n", type=int, default=0, help="size override for --workload large")
     ap.add_argument("--cpu-pairs", type=int, default=100)
