@@ -6,12 +6,14 @@ package never imports it, and it imports nothing from the product package.
 """
 from .fram_oracle import (DEFAULTS, DegenerateError, FRAResult, FramResult, InvalidInputError,
                           SDSNResult, accuracy, damped_update, fra_exact, fra_residual, fram,
-                          gamma, simplex_thresholds, gradient, initial_assignment,
+                          gamma, simplex_thresholds, gradient, gradient_columns,
+                          initial_assignment,
                           lap_max, matching_error, node_affinity, objective, p1, p2, p3,
                           prescale, sdsn, validate)
 
 __all__ = ["DEFAULTS", "DegenerateError", "FRAResult", "fra_exact", "fra_residual",
            "simplex_thresholds", "FramResult", "InvalidInputError", "SDSNResult",
-           "accuracy", "damped_update", "fram", "gamma", "gradient", "initial_assignment",
+           "accuracy", "damped_update", "fram", "gamma", "gradient", "gradient_columns",
+           "initial_assignment",
            "lap_max", "matching_error", "node_affinity", "objective", "p1", "p2", "p3", "prescale", "sdsn",
            "validate"]

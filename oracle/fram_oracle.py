@@ -109,6 +109,17 @@ def gradient(A, N, B, K=None, lam=1.0):
     return X
 
 
+def gradient_columns(A, N, B, cols, K=None, lam=1.0):
+    """Columns `cols` of the same X (eq. 3), each as A (N B[:, j]) + lambda
+    K[:, j]: two matrix-vector products per column, for sampled checks at
+    sizes where the full n^3 product is too slow on the CPU."""
+    cols = np.asarray(cols, dtype=np.int64)
+    X = A @ (N @ B[:, cols])
+    if K is not None:
+        X = X + lam * K[:, cols]
+    return X
+
+
 # --------------------------------------------------------------------------
 # Eq. 7: the two projections that SDSN alternates.
 #   P1(X) = X + (I/n + (1^T X 1/n^2) I - X/n) 1 1^T - 1 1^T X / n

@@ -293,6 +293,24 @@ def test_gradient_is_derivative_of_objective():
         assert abs(fd - G[i, j]) < 1e-7
 
 
+def test_gradient_columns_equal_the_finite_difference_pinned_gradient():
+    # The column form is the same X: checked against gradient() (pinned above
+    # by finite differences) and against the written-out triple sum.
+    n = 9
+    rng = np.random.default_rng(5)
+    A = rand_mat(n, 4, asym=False)
+    B = rand_mat(n, 5, asym=False)
+    K = rng.random((n, n))
+    N = rng.random((n, n))
+    cols = [0, 3, 8, 3]
+    Xc = o.gradient_columns(A, N, B, cols, K, 0.7)
+    assert np.allclose(Xc, o.gradient(A, N, B, K, 0.7)[:, cols], rtol=1e-14, atol=0)
+    j = 8
+    direct = [sum(A[i, k] * N[k, l] * B[l, j] for k in range(n) for l in range(n)) + 0.7 * K[i, j]
+              for i in range(n)]
+    assert np.allclose(Xc[:, 2], direct, rtol=1e-13, atol=0)
+
+
 # ------------------------------------------------- Alg. 1 steps 7-8
 def test_damped_update_delta_closed_form():
     # alpha = 1 from N = 11^T/n to D = I: ||I - J/n||_F^2 = n - 1, ||I||_F^2 = n.
