@@ -647,6 +647,155 @@ struct CandSlot {
   double h;  // -(W[i][j] + v_j) - label of the candidate: the next step's h
 };
 
+// Column state of one CTA of a cluster completion, in its shared memory.
+struct ColState {
+  unsigned long long* dkey;  // label keys (kVisited once popped)
+  unsigned long long* tkey;  // test keys; the label bits once popped
+  double* v;                 // potentials
+  double* wmat;              // W[colrow[j]][j], kept in step with colrow
+  int* colrow;
+};
+
+__device__ __forceinline__ ColState col_state(unsigned char* sm, int S) {
+  ColState c;
+  c.dkey = reinterpret_cast<unsigned long long*>(sm);
+  c.tkey = c.dkey + S;
+  c.v = reinterpret_cast<double*>(c.tkey + S);
+  c.wmat = c.v + S;
+  c.colrow = reinterpret_cast<int*>(c.wmat + S);
+  return c;
+}
+
+// First relaxation from the free row f: labels -(W_fj + v_j) for this CTA's
+// columns [jb, jb + ns) and this thread's best (label key, tie key).
+__device__ __forceinline__ void relax_first(const double* __restrict__ rowf, int f, int n, int jb,
+                                            int ns, const ColState& c, int* pred,
+                                            unsigned long long& best, int& bk) {
+  best = kVisited;
+  bk = 0x7fffffff;
+  for (int jl = threadIdx.x; jl < ns; jl += kClusterThreads) {
+    const int j = jb + jl;
+    const double x = rowf[j];
+    const unsigned long long dk = okey(-(x + c.v[jl]));
+    c.dkey[jl] = dk;
+    c.tkey[jl] = okey(x);
+    pred[j] = f;
+    const int kk = c.colrow[jl] == -1 ? j : j + n;
+    if (dk < best || (dk == best && kk < bk)) {
+      best = dk;
+      bk = kk;
+    }
+  }
+}
+
+// One Dijkstra step's relaxation with row i (shift h) over this CTA's
+// unvisited columns, and this thread's best candidate afterwards.
+__device__ __forceinline__ void relax_row(const double* __restrict__ rowi, double h, int i, int n,
+                                          int jb, int ns, const ColState& c, int* pred,
+                                          unsigned long long& best, int& bk) {
+  const int tid = threadIdx.x;
+  double wv[kSolveUnroll];
+  const bool pre = ns <= kSolveUnroll * kClusterThreads;
+  if (pre) {
+#pragma unroll
+    for (int u = 0; u < kSolveUnroll; ++u) {
+      const int jl = tid + u * kClusterThreads;
+      if (jl < ns) wv[u] = rowi[jb + jl];
+    }
+  }
+  best = kVisited;
+  bk = 0x7fffffff;
+  for (int base = tid; base < ns; base += kSolveUnroll * kClusterThreads) {
+    if (!pre || base != tid) {
+#pragma unroll
+      for (int u = 0; u < kSolveUnroll; ++u) {
+        const int jl = base + u * kClusterThreads;
+        if (jl < ns) wv[u] = rowi[jb + jl];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSolveUnroll; ++u) {
+      const int jl = base + u * kClusterThreads;
+      if (jl >= ns) continue;
+      unsigned long long dk = c.dkey[jl];
+      if (dk == kVisited) continue;
+      const double x = wv[u] + h;
+      const unsigned long long xk = okey(x);
+      if (xk > c.tkey[jl]) {  // W_ij + h > t_j: a shorter path to column j
+        c.tkey[jl] = xk;
+        const unsigned long long nk = okey(-(x + c.v[jl]));
+        if (nk < dk) {
+          dk = nk;
+          c.dkey[jl] = nk;
+          pred[jb + jl] = i;
+        }
+      }
+      const int kk = c.colrow[jl] == -1 ? jb + jl : jb + jl + n;
+      if (dk < best || (dk == best && kk < bk)) {
+        best = dk;
+        bk = kk;
+      }
+    }
+  }
+}
+
+// The cluster-wide winner: each warp's best candidate into its slot; after
+// the cluster barrier warp 0 of every CTA reads all kLapCluster x 8 slots
+// through distributed shared memory (two per lane), reduces them by the
+// same integer comparison and broadcasts through *s_win.  Slots are double-
+// buffered by exchange parity (`par`): a slot is written again only two
+// cluster barriers after the last remote read of it.
+__device__ __forceinline__ CandSlot cluster_exchange(cg::cluster_group& cl, int cr, int n, int jb,
+                                                     const ColState& c,
+                                                     CandSlot (*slots)[kClusterWarps],
+                                                     CandSlot* s_win, int& par,
+                                                     unsigned long long best, int bk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
+    const int ok2 = __shfl_xor_sync(0xffffffffu, bk, o);
+    if (ok < best || (ok == best && ok2 < bk)) {
+      best = ok;
+      bk = ok2;
+    }
+  }
+  if (lane == 0) {
+    CandSlot cs{best, bk, -2, 0.0};
+    if (best != kVisited && bk < 2 * n) {  // a column of this warp: stable during the step
+      const int jl = (bk >= n ? bk - n : bk) - jb;
+      cs.i = c.colrow[jl];
+      cs.h = -(c.wmat[jl] + c.v[jl]) - okey_value(best);
+    }
+    slots[par][warp] = cs;
+  }
+  cl.sync();
+  if (warp == 0) {
+    // Lane l: slot l % 8 of CTAs l / 8 and l / 8 + 4.
+    const CandSlot c0 = *cl.map_shared_rank(&slots[par][lane & 7], lane >> 3);
+    const CandSlot c1 = *cl.map_shared_rank(&slots[par][lane & 7], (lane >> 3) + 4);
+    CandSlot r = c0;
+    if (c1.key < r.key || (c1.key == r.key && c1.k < r.k)) r = c1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, r.key, o);
+      const int ok2 = __shfl_xor_sync(0xffffffffu, r.k, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, r.i, o);
+      const double oh = __shfl_xor_sync(0xffffffffu, r.h, o);
+      if (ok < r.key || (ok == r.key && ok2 < r.k)) {
+        r.key = ok;
+        r.k = ok2;
+        r.i = oi;
+        r.h = oh;
+      }
+    }
+    if (lane == 0) *s_win = r;
+  }
+  __syncthreads();
+  par ^= 1;
+  return *s_win;
+}
+
 __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     const double* __restrict__ W, int ldw, int n, LapWs w, int pass, long long budget,
     int32_t* __restrict__ perm, LapStats* st) {
@@ -656,21 +805,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
   const int S = (n + kLapCluster - 1) / kLapCluster;
   const int jb = min(n, cr * S), ns = min(n, jb + S) - jb;
   extern __shared__ __align__(16) unsigned char lap_sm[];
-  unsigned long long* dkey = reinterpret_cast<unsigned long long*>(lap_sm);
-  unsigned long long* tkey = dkey + S;
-  double* v = reinterpret_cast<double*>(tkey + S);
-  double* wmat = v + S;  // W[colrow[j]][j], kept in step with colrow
-  int* colrow = reinterpret_cast<int*>(wmat + S);
+  const ColState c = col_state(lap_sm, S);
   __shared__ CandSlot slots[2][kClusterWarps];
   __shared__ CandSlot s_win;
   __shared__ int s_aug;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int* pred = w.way;
   for (int jl = tid; jl < ns; jl += kClusterThreads) {
-    v[jl] = w.v[jb + jl];
+    c.v[jl] = w.v[jb + jl];
     const int r = w.colrow[jb + jl];
-    colrow[jl] = r;
-    wmat[jl] = r >= 0 ? W[(size_t)r * ldw + jb + jl] : 0.0;
+    c.colrow[jl] = r;
+    c.wmat[jl] = r >= 0 ? W[(size_t)r * ldw + jb + jl] : 0.0;
   }
   if (tid == 0) {
     s_aug = 0;
@@ -680,142 +825,32 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     }
   }
   int par = 0;
-  // This warp's best candidate into its slot, then (warp 0 of each CTA) the
-  // cluster-wide winner over all slots, broadcast through s_win.
-  auto exchange = [&](unsigned long long best, int bk, unsigned long long& key, int& k, int& i,
-                      double& h) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, best, o);
-      const int ok2 = __shfl_xor_sync(0xffffffffu, bk, o);
-      if (ok < best || (ok == best && ok2 < bk)) {
-        best = ok;
-        bk = ok2;
-      }
-    }
-    if (lane == 0) {
-      CandSlot c{best, bk, -2, 0.0};
-      if (best != kVisited && bk < 2 * n) {  // a column of this warp: stable during the step
-        const int jl = (bk >= n ? bk - n : bk) - jb;
-        c.i = colrow[jl];
-        c.h = -(wmat[jl] + v[jl]) - okey_value(best);
-      }
-      slots[par][warp] = c;
-    }
-    cl.sync();
-    if (warp == 0) {
-      // Lane l: slot l % 8 of CTAs l / 8 and l / 8 + 4.
-      const CandSlot c0 = *cl.map_shared_rank(&slots[par][lane & 7], lane >> 3);
-      const CandSlot c1 = *cl.map_shared_rank(&slots[par][lane & 7], (lane >> 3) + 4);
-      CandSlot c = c0;
-      if (c1.key < c.key || (c1.key == c.key && c1.k < c.k)) c = c1;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, c.key, o);
-        const int ok2 = __shfl_xor_sync(0xffffffffu, c.k, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, c.i, o);
-        const double oh = __shfl_xor_sync(0xffffffffu, c.h, o);
-        if (ok < c.key || (ok == c.key && ok2 < c.k)) {
-          c.key = ok;
-          c.k = ok2;
-          c.i = oi;
-          c.h = oh;
-        }
-      }
-      if (lane == 0) s_win = c;
-    }
-    __syncthreads();
-    key = s_win.key;
-    k = s_win.k;
-    i = s_win.i;
-    h = s_win.h;
-    par ^= 1;
-  };
   cl.sync();
 
   long long total = 0;
   for (int f = 0; f < n; ++f) {
     if (w.rowcol[f] != -1) continue;  // uniform: written before the last cluster barrier
-    const double* rowf = W + (size_t)f * ldw;
-    unsigned long long best = kVisited;
-    int bk = 0x7fffffff;
-    for (int jl = tid; jl < ns; jl += kClusterThreads) {
-      const int j = jb + jl;
-      const double x = rowf[j];
-      const unsigned long long dk = okey(-(x + v[jl]));
-      dkey[jl] = dk;
-      tkey[jl] = okey(x);
-      pred[j] = f;
-      const int kk = colrow[jl] == -1 ? j : j + n;
-      if (dk < best || (dk == best && kk < bk)) {
-        best = dk;
-        bk = kk;
-      }
-    }
-    unsigned long long key;
-    int k, i;
-    double h;
-    exchange(best, bk, key, k, i, h);
-    double mu = okey_value(key);
+    unsigned long long best;
+    int bk;
+    relax_first(W + (size_t)f * ldw, f, n, jb, ns, c, pred, best, bk);
+    CandSlot win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
+    double mu = okey_value(win.key);
     int steps = 0, j1;
     while (true) {
-      if (k < 0 || k >= 2 * n || key == kVisited) {  // no finite label left (all CTAs)
+      if (win.k < 0 || win.k >= 2 * n || win.key == kVisited) {  // no finite label left (all CTAs)
         if (cr == 0 && tid == 0) st->status = 1;
         cl.sync();  // no CTA leaves while another may still read its slot
         return;
       }
-      j1 = k >= n ? k - n : k;
+      j1 = win.k >= n ? win.k - n : win.k;
       if (j1 >= jb && j1 < jb + ns && (j1 - jb) % kClusterThreads == tid) {
-        tkey[j1 - jb] = (unsigned long long)__double_as_longlong(mu);
-        dkey[j1 - jb] = kVisited;
+        c.tkey[j1 - jb] = (unsigned long long)__double_as_longlong(mu);
+        c.dkey[j1 - jb] = kVisited;
       }
-      if (i == -1) break;  // j1 is free: augment
-      const double* rowi = W + (size_t)i * ldw;
-      double wv[kSolveUnroll];
-      const bool pre = ns <= kSolveUnroll * kClusterThreads;
-      if (pre) {
-#pragma unroll
-        for (int u = 0; u < kSolveUnroll; ++u) {
-          const int jl = tid + u * kClusterThreads;
-          if (jl < ns) wv[u] = rowi[jb + jl];
-        }
-      }
-      best = kVisited;
-      bk = 0x7fffffff;
-      for (int base = tid; base < ns; base += kSolveUnroll * kClusterThreads) {
-        if (!pre || base != tid) {
-#pragma unroll
-          for (int u = 0; u < kSolveUnroll; ++u) {
-            const int jl = base + u * kClusterThreads;
-            if (jl < ns) wv[u] = rowi[jb + jl];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kSolveUnroll; ++u) {
-          const int jl = base + u * kClusterThreads;
-          if (jl >= ns) continue;
-          unsigned long long dk = dkey[jl];
-          if (dk == kVisited) continue;
-          const double x = wv[u] + h;
-          const unsigned long long xk = okey(x);
-          if (xk > tkey[jl]) {
-            tkey[jl] = xk;
-            const unsigned long long nk = okey(-(x + v[jl]));
-            if (nk < dk) {
-              dk = nk;
-              dkey[jl] = nk;
-              pred[jb + jl] = i;
-            }
-          }
-          const int kk = colrow[jl] == -1 ? jb + jl : jb + jl + n;
-          if (dk < best || (dk == best && kk < bk)) {
-            best = dk;
-            bk = kk;
-          }
-        }
-      }
-      exchange(best, bk, key, k, i, h);
-      mu = okey_value(key);
+      if (win.i == -1) break;  // j1 is free: augment
+      relax_row(W + (size_t)win.i * ldw, win.h, win.i, n, jb, ns, c, pred, best, bk);
+      win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
+      mu = okey_value(win.key);
       ++total;
       if (++steps > n) {
         if (cr == 0 && tid == 0) st->status = 1;
@@ -830,7 +865,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     }
     // Potentials of the popped columns, then (CTA 0) flip the path.
     for (int jl = tid; jl < ns; jl += kClusterThreads)
-      if (dkey[jl] == kVisited) v[jl] += __longlong_as_double((long long)tkey[jl]) - mu;
+      if (c.dkey[jl] == kVisited) c.v[jl] += __longlong_as_double((long long)c.tkey[jl]) - mu;
     cl.sync();  // every CTA's pred writes and potentials are done
     if (cr == 0 && tid == 0) {
       int j = j1;
@@ -838,8 +873,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
         const int r = pred[j];
         const int prev = w.rowcol[r];
         const int owner = j / S;
-        int* rc = cl.map_shared_rank(colrow, owner);
-        double* rw = cl.map_shared_rank(wmat, owner);
+        int* rc = cl.map_shared_rank(c.colrow, owner);
+        double* rw = cl.map_shared_rank(c.wmat, owner);
         rc[j - owner * S] = r;
         rw[j - owner * S] = W[(size_t)r * ldw + j];
         w.rowcol[r] = j;
