@@ -129,7 +129,8 @@ constexpr int kListCap = 256;
 template <int C>
 __device__ double warp_threshold_reg(const double* __restrict__ y, const double* v, int n,
                                      bool cold, double w0, double* res,
-                                     unsigned long long* __restrict__ list) {
+                                     unsigned long long* __restrict__ list,
+                                     const double* __restrict__ rinv) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long zk[C];
@@ -152,7 +153,7 @@ __device__ double warp_threshold_reg(const double* __restrict__ y, const double*
     zmax = oz > zmax ? oz : zmax;
   }
   double a = w0;
-  if (cold) a = (warp_sum(s) - 1.0) / n;
+  if (cold) a = (warp_sum(s) - 1.0) * rinv[n];
   int m = -1;                   // list length (-1: no list)
   unsigned long long lkey = 0;  // key of the a the list was built at
   int kprev = -1;
@@ -208,7 +209,7 @@ __device__ double warp_threshold_reg(const double* __restrict__ y, const double*
       kprev = -1;
       continue;
     }
-    a = (S - 1.0) / k;
+    a = (S - 1.0) * rinv[k];  // within an ulp of the quotient; no FP64 divide
   }
   return a;
 }
@@ -217,19 +218,22 @@ __device__ double warp_threshold_reg(const double* __restrict__ y, const double*
 template <int C>
 __device__ __forceinline__ double threshold(const double* __restrict__ y, const double* v, int n,
                                             bool cold, double w0, double* res,
-                                            unsigned long long* list) {
+                                            unsigned long long* list, const double* rinv) {
   if constexpr (C == 0)
     return warp_threshold(y, v, n, cold, w0, res);
   else
-    return warp_threshold_reg<C>(y, v, n, cold, w0, res, list);
+    return warp_threshold_reg<C>(y, v, n, cold, w0, res, list, rinv);
 }
 
 // Dynamic shared memory: a and b (n doubles each), then with C > 0 one
-// key list per warp.
+// key list per warp and the reciprocals 1/k, k = 0..n (FP64 division is a
+// long instruction sequence on this GPU; each Newton step needs one).
 template <int C>
 size_t fra_smem_bytes(int n) {
   return 2 * (size_t)n * sizeof(double) +
-         (C > 0 ? (size_t)kFraWarps * kListCap * sizeof(unsigned long long) : 0);
+         (C > 0 ? (size_t)kFraWarps * kListCap * sizeof(unsigned long long) +
+                      (size_t)(n + 1) * sizeof(double)
+                : 0);
 }
 
 template <int C>
@@ -241,8 +245,9 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
   double* a_s = fra_sm;
   double* b_s = fra_sm + n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned long long* list =
-      reinterpret_cast<unsigned long long*>(fra_sm + 2 * (size_t)n) + (size_t)warp * kListCap;
+  unsigned long long* lists = reinterpret_cast<unsigned long long*>(fra_sm + 2 * (size_t)n);
+  unsigned long long* list = lists + (size_t)warp * kListCap;
+  double* rinv = reinterpret_cast<double*>(lists + (size_t)kFraWarps * kListCap);  // C > 0 only
   const int G = gridDim.x, blk = blockIdx.x;
   const int R = (n + G - 1) / G;
   const int i0 = min(n, blk * R), i1 = min(n, i0 + R);
@@ -273,6 +278,8 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
     for (int i = lane; i < n; i += 32) trow[i] = __ldcg(p.Y + (size_t)i * p.ldy + j);
   }
   for (int j = tid; j < n; j += kFraThreads) b_s[j] = 0.0;
+  if (C > 0)
+    for (int q = tid; q <= n; q += kFraThreads) rinv[q] = q > 0 ? 1.0 / q : 0.0;
   __syncthreads();
 
   double omega = 1.0, prev_res = INFINITY, rowres = INFINITY;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
     for (int i = i0 + warp; i < i1; i += kFraWarps) {
       double r = 0.0;
       const double w0 = k > 0 ? a_cur[i] : 0.0;
-      const double t = threshold<C>(p.Y + (size_t)i * p.ldy, b_s, n, k == 0, w0, &r, list);
+      const double t = threshold<C>(p.Y + (size_t)i * p.ldy, b_s, n, k == 0, w0, &r, list, rinv);
       if (lane == 0) a_new[i] = k > 0 ? w0 + omega * (t - w0) : t;
       lres = fmax(lres, r);
     }
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(kFraThreads) fra_kernel(FraK p) {
     for (int j = i0 + warp; j < i1; j += kFraWarps) {
       double r = 0.0;
       const double w0 = b_s[j];
-      const double t = threshold<C>(p.Yt + (size_t)j * p.ldt, a_s, n, k == 0, w0, &r, list);
+      const double t = threshold<C>(p.Yt + (size_t)j * p.ldt, a_s, n, k == 0, w0, &r, list, rinv);
       if (lane == 0) p.bv[j] = k > 0 ? w0 + w_col * (t - w0) : t;
     }
     col_plain = k == 0 || w_col == 1.0;
