@@ -619,23 +619,24 @@ struct BatchedState {
 
 template <typename T>
 void set_attrs() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(batched_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batched_smem_bytes<T>(128));
-  cudaFuncSetAttribute(batched_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batched_smem_bytes<T>(256));
-  cudaFuncSetAttribute(batched_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batched_smem_bytes<T>(512));
-  done = true;
+  static DeviceCache done;
+  device_cached(done, [] {
+    cudaFuncSetAttribute(batched_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batched_smem_bytes<T>(128));
+    cudaFuncSetAttribute(batched_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batched_smem_bytes<T>(256));
+    cudaFuncSetAttribute(batched_kernel<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batched_smem_bytes<T>(512));
+    return 1;
+  });
 }
 
 // Resident CTAs per SM for a block size (queried once).
 template <typename T>
 int batched_occupancy(int nt) {
-  static int occ[3] = {0, 0, 0};
+  static DeviceCache occ[3];
   const int k = nt == 128 ? 0 : (nt == 256 ? 1 : 2);
-  if (occ[k] == 0) {
+  return device_cached(occ[k], [nt] {
     int v = 0;
     cudaError_t e =
         nt == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_kernel<T, 128>, 128,
@@ -644,9 +645,8 @@ int batched_occupancy(int nt) {
                                                                     batched_smem_bytes<T>(256))
                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_kernel<T, 512>, 512,
                                                                     batched_smem_bytes<T>(512));
-    occ[k] = (e == cudaSuccess && v > 0) ? v : 1;
-  }
-  return occ[k];
+    return (e == cudaSuccess && v > 0) ? v : 1;
+  });
 }
 
 template <typename T>

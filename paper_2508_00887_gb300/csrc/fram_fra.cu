@@ -360,13 +360,14 @@ namespace {
 template <int C>
 int launch_fra_c(const FraK& k, int n, int num_sms, cudaStream_t s) {
   const size_t smem = fra_smem_bytes<C>(n);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(fra_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             216 * 1024) != cudaSuccess)
-      return -1;
-    attr = true;
-  }
+  static DeviceCache attr;
+  if (device_cached(attr, [] {
+        return cudaFuncSetAttribute(fra_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    216 * 1024) == cudaSuccess
+                   ? 1
+                   : -1;
+      }) < 0)
+    return -1;
   // Occupancy depends on smem (n); query it for each launch size.
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fra_kernel<C>, kFraThreads, smem) !=

@@ -418,26 +418,28 @@ bool make_map(CUtensorMap* m, const void* ptr, int ld, int kind, int box_rows) {
 namespace {
 
 int num_sms_cached() {
-  static int v = 0;
-  if (v == 0) {
-    int dev = 0;
+  static DeviceCache cache;
+  return device_cached(cache, [] {
+    int dev = 0, v = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
       v = 1;
-  }
-  return v;
+    return v;
+  });
 }
 
 template <int KIND, int BN>
 int launch_k(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, int ld,
              cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(gemm_tc_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg<BN>::SMEM_BYTES) != cudaSuccess)
-      return -1;
-    attr = true;
-  }
+  static DeviceCache attr;
+  if (device_cached(attr, [] {
+        return cudaFuncSetAttribute(gemm_tc_kernel<KIND, BN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cfg<BN>::SMEM_BYTES) == cudaSuccess
+                   ? 1
+                   : -1;
+      }) < 0)
+    return -1;
   const int ntiles = (ld / BM) * ((ld + BN - 1) / BN);
   const int grid = ntiles < num_sms_cached() ? ntiles : num_sms_cached();
   gemm_tc_kernel<KIND, BN><<<grid, GEMM_THREADS, Cfg<BN>::SMEM_BYTES, s>>>(ma, mb, g);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace fram {
 
 // Device-side status codes (written into a status word by kernels).
@@ -12,6 +14,28 @@ enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_DEGENERATE = 2 };
 
 // Default limit for every device-side wait (grid barriers, flags).
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s
+
+// ------------------------------------------------------------ host helpers
+// A launch fact computed once per device (a kernel attribute set, an
+// occupancy, the SM count): function attributes are per device, and several
+// contexts -- on several devices, or the serving thread beside the caller's
+// -- may ask at once.  compute() returns the value to keep; 0 means "not
+// computed" and is never kept.
+constexpr int kMaxDevices = 64;
+
+struct DeviceCache {
+  std::mutex mu;
+  int val[kMaxDevices] = {};
+};
+
+template <typename F>
+int device_cached(DeviceCache& c, F compute) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (c.val[dev] == 0) c.val[dev] = compute();
+  return c.val[dev];
+}
 
 // ------------------------------------------------------------ device helpers
 __device__ __forceinline__ uint64_t globaltimer_ns() {

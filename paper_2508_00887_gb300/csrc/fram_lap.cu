@@ -939,17 +939,17 @@ int auction_threads(int n) {
 
 int launch_auction(const double* W, int ldw, int n, LapWs w, int num_sms, uint64_t limit_ns,
                    cudaStream_t s) {
-  static int per_sm[11] = {};  // by log2(threads)
+  static DeviceCache per_sm[11];  // by log2(threads)
   const int t = auction_threads(n);
   const int lg = 31 - __builtin_clz((unsigned)t);
-  if (per_sm[lg] == 0) {
+  const int occ = device_cached(per_sm[lg], [t] {
     int v = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, lap_auction_kernel, t, 0) != cudaSuccess)
       return -1;
-    per_sm[lg] = v > 0 ? v : -1;
-  }
-  if (per_sm[lg] < 0 || num_sms < 1) return -1;
-  int blocks = per_sm[lg] * num_sms;
+    return v > 0 ? v : -1;
+  });
+  if (occ < 0 || num_sms < 1) return -1;
+  int blocks = occ * num_sms;
   if (blocks > n) blocks = n;
   void* args[] = {(void*)&W, (void*)&ldw, (void*)&n, (void*)&w, (void*)&limit_ns};
   if (cudaLaunchCooperativeKernel((const void*)lap_auction_kernel, dim3(blocks), dim3(t), args,
@@ -964,15 +964,17 @@ namespace {
 
 // Can a cluster of kLapCluster CTAs with `smem` bytes each be resident?
 bool cluster_ok(size_t smem) {
-  static size_t set_for = 0;
-  if (set_for < smem) {
-    if (cudaFuncSetAttribute(lap_solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSolveSmemCap) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
-    set_for = kSolveSmemCap;
-  }
+  static DeviceCache attr;
+  if (device_cached(attr, [] {
+        if (cudaFuncSetAttribute(lap_solve_cluster_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSolveSmemCap) != cudaSuccess) {
+          cudaGetLastError();
+          return -1;
+        }
+        return 1;
+      }) < 0)
+    return false;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(kLapCluster);
   cfg.blockDim = dim3(kClusterThreads);
@@ -1012,13 +1014,15 @@ int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, voi
   if (rblocks > 2368) rblocks = 2368;
   const size_t sm = solve_smem_bytes(n);
   const int use_smem = sm <= kSolveSmemCap;
-  static bool attr_set = false;
-  if (use_smem && !attr_set) {
-    if (cudaFuncSetAttribute(lap_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSolveSmemCap) != cudaSuccess)
-      return -1;
-    attr_set = true;
-  }
+  static DeviceCache attr;
+  if (use_smem && device_cached(attr, [] {
+                    return cudaFuncSetAttribute(lap_solve_kernel,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)kSolveSmemCap) == cudaSuccess
+                               ? 1
+                               : -1;
+                  }) < 0)
+    return -1;
   const size_t dsm = use_smem ? sm : 0;
   // The cluster completion for large n (its column state fits on chip up to
   // n = 8 x 7,800); the one-CTA kernel below that.

@@ -493,8 +493,9 @@ void set_vec_flags(SdsnK<T, TIn>& k) {
 
 template <typename T, typename TIn, int MAXC>
 int launch_k(SdsnK<T, TIn>& k, int nblocks, size_t smem, int num_sms, cudaStream_t s) {
-  static int per_sm = -1;  // occupancy does not depend on the (capped) smem size here
-  if (per_sm < 0) {
+  // Occupancy does not depend on the (capped) smem size here.
+  static DeviceCache cache;
+  const int per_sm = device_cached(cache, [] {
     if (cudaFuncSetAttribute(sdsn_kernel<T, TIn, MAXC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) !=
         cudaSuccess)
@@ -503,8 +504,8 @@ int launch_k(SdsnK<T, TIn>& k, int nblocks, size_t smem, int num_sms, cudaStream
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sdsn_kernel<T, TIn, MAXC>, kSdsnThreads,
                                                       kSmemCap) != cudaSuccess)
       return -1;
-    per_sm = v;
-  }
+    return v > 0 ? v : -1;
+  });
   if (per_sm < 1 || nblocks > per_sm * num_sms) return -1;
   void* args[] = {&k};
   if (cudaLaunchCooperativeKernel((const void*)sdsn_kernel<T, TIn, MAXC>, dim3(nblocks),
@@ -560,8 +561,8 @@ static_assert(sizeof(SdsnK<double, double>) <= 256, "group descriptor slot");
 template <typename T, typename TIn, int MAXC>
 int launch_group_k(const SdsnK<T, TIn>* dprobs, int nprobs, int nblocks, size_t smem,
                    int num_sms, cudaStream_t s) {
-  static int per_sm = -1;
-  if (per_sm < 0) {
+  static DeviceCache cache;
+  const int per_sm = device_cached(cache, [] {
     if (cudaFuncSetAttribute(sdsn_group_kernel<T, TIn, MAXC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) !=
         cudaSuccess)
@@ -570,8 +571,8 @@ int launch_group_k(const SdsnK<T, TIn>* dprobs, int nprobs, int nblocks, size_t 
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sdsn_group_kernel<T, TIn, MAXC>,
                                                       kSdsnThreads, kSmemCap) != cudaSuccess)
       return -1;
-    per_sm = v;
-  }
+    return v > 0 ? v : -1;
+  });
   if (per_sm < 1 || nblocks > per_sm * num_sms) return -1;
   void* args[] = {(void*)&dprobs, &nprobs};
   if (cudaLaunchCooperativeKernel((const void*)sdsn_group_kernel<T, TIn, MAXC>, dim3(nblocks),

@@ -57,7 +57,6 @@ struct StaticHeader {
 };
 static_assert(sizeof(StaticHeader) <= kHeaderBytes, "header does not fit");
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
