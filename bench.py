@@ -682,7 +682,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     where no capture covers the size:
       n = 1000: 4.16 MB per launch, whatever the sweep count: the tiles stay
         in shared memory and only X is read (capture of this workload);
-      n >= 6144 (the matrix far above L2): 7.85 bytes per element per pass,
+      n >= 6144 (the matrix far above L2): 7.80 bytes per element per pass,
         measured at n = 6144 (59.16 GB over 201 passes of 6144^2), scaled to
         n^2 (sweeps + 1) bytes."""
     if s != 4:
@@ -690,7 +690,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     if n == 1000:
         return 4.16e6
     if n >= 6144:
-        return 7.85 * n * n * (sweeps_per_launch + 1.0)
+        return 7.80 * n * n * (sweeps_per_launch + 1.0)
     return None
 
 

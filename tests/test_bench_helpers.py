@@ -1,0 +1,40 @@
+"""The bench line's roofline arithmetic (CPU only): the measured DRAM bytes
+per SDSN launch and how they scale, the batched kernel's ALU roofline, and
+the job rate."""
+from types import SimpleNamespace
+
+import pytest
+
+import bench
+
+
+def test_sdsn_traffic_measured_and_scaled():
+    # n = 1000: the ncu figure, independent of the sweep count (on chip).
+    assert bench.sdsn_traffic(1000, 4, 196.0) == 4.16e6
+    assert bench.sdsn_traffic(1000, 4, 10.0) == 4.16e6
+    # n >= 6144: bytes per element and pass times n^2 (sweeps + 1); at the
+    # captured size and sweep count it gives back the capture (59.16 GB).
+    t = bench.sdsn_traffic(6144, 4, 200.0)
+    assert t == pytest.approx(59.16e9, rel=2e-3)
+    assert bench.sdsn_traffic(8192, 4, 200.0) == pytest.approx(t * (8192 / 6144) ** 2)
+    # no capture covers these: reported as null
+    assert bench.sdsn_traffic(4039, 4, 200.0) is None
+    assert bench.sdsn_traffic(1000, 8, 200.0) is None
+
+
+def test_batch_roofline_counts_algorithmic_flops():
+    ns = [10, 64]
+    infos = [SimpleNamespace(outer_iters=2, total_sweeps=30),
+             SimpleNamespace(outer_iters=1, total_sweeps=5)]
+    flops = (2 * (4 * 10 ** 3 + 6 * 10 ** 2) + 30 * 7 * 10 ** 2
+             + 1 * (4 * 64 ** 3 + 6 * 64 ** 2) + 5 * 7 * 64 ** 2)
+    r = bench.batch_roofline(ns, infos, 1e-3)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_job_rate_is_units_of_all_ranks_over_the_slowest():
+    assert bench.job_rate(10, 1, 2.0) == pytest.approx(5.0)
+    assert bench.job_rate(10, 4, 2.0) == pytest.approx(20.0)
