@@ -252,6 +252,24 @@ fram_status fram_gradient_lowp(fram_ctx *ctx, int n, const double *A, const doub
 fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double theta,
                       double gamma_tol, int max_sweeps, int *sweeps_out, double *gamma_out);
 
+/* SDSN (Alg. 2) as the mixed paths run it (Alg. 1 step 6 in FP32, Sec. 6
+ * "Mixed-precision architecture"): the same kernel and launch configuration
+ * as the FP32 phase inside fram_solve, on FP32 data.
+ *   X  n x n FP32 device array, row stride ldx >= n elements (read only
+ *      unless D == X)
+ *   D  n x n FP32 device array, row stride ldd >= n (D == X allowed, then
+ *      ldd == ldx); the padding columns of either are not touched
+ * D0 = (theta/2) X / max(X) (max taken over the n x n block); every sweep
+ * D <- max(0, P1(D)) (eq. 7) in FP32 arithmetic with FP32 row and column
+ * sums; the total S and gamma = S/n - 1 are formed in FP64 from FP32 tile
+ * totals; stop when gamma <= gamma_tol (after at least one sweep) or after
+ * max_sweeps sweeps.  sweeps_out / gamma_out (host) may be NULL.
+ * Errors: FRAM_ERR_INVALID (bad sizes, strides or pointers),
+ * FRAM_ERR_DEGENERATE (max(X) <= 0), FRAM_ERR_TIMEOUT, FRAM_ERR_CUDA. */
+fram_status fram_sdsn_f32(fram_ctx *ctx, int n, const float *X, int ldx, float *D, int ldd,
+                          double theta, double gamma_tol, int max_sweeps, int *sweeps_out,
+                          double *gamma_out);
+
 /* Exact FRA projection (eq. 4 / Thm. 1; a variant of Alg. 1 step 6, not in
  * the paper): D = argmin over doubly stochastic D of ||D - (theta/2) X/max X||_F,
  * computed as D = max(0, Y0 - a 1^T - 1 b^T) by block coordinate ascent on

@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "fram_set_sparse_density": (i, [_P, d]),
         "fram_gradient_lowp": (i, [_P, i, _P, _P, _P, _P, d, i, _P]),
         "fram_sdsn": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
+        "fram_sdsn_f32": (i, [_P, i, _P, i, _P, i, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
         "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d), C.POINTER(i)]),
         "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
@@ -116,7 +117,7 @@ def exported_symbols():
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
             "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_grouped",
+            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_f32", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
 
@@ -265,6 +266,19 @@ def fram_sdsn(ctx, n, X, D, theta, gamma_tol=1e-14, max_sweeps=200, check=True):
     g = C.c_double()
     st = load().fram_sdsn(ctx, n, _addr(X), _addr(D), theta, gamma_tol, max_sweeps, C.byref(sw),
                           C.byref(g))
+    if check:
+        _check(ctx, st)
+    return st, sw.value, g.value
+
+
+def fram_sdsn_f32(ctx, n, X, D, theta, gamma_tol=1e-6, max_sweeps=200, ldx=None, ldd=None,
+                  check=True):
+    """FP32 SDSN (the mixed paths' kernel) on float32 device buffers with row
+    strides ldx / ldd (default n)."""
+    sw = C.c_int()
+    g = C.c_double()
+    st = load().fram_sdsn_f32(ctx, n, _addr(X, "float32"), ldx or n, _addr(D, "float32"),
+                              ldd or n, theta, gamma_tol, max_sweeps, C.byref(sw), C.byref(g))
     if check:
         _check(ctx, st)
     return st, sw.value, g.value

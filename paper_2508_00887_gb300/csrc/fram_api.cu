@@ -33,6 +33,14 @@ void set_err(fram_ctx* c, const char* fmt, ...) {
 }
 
 fram_status cuda_fail(fram_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) {
+    // A launcher refused without a CUDA error: the launch would exceed a
+    // limit of this GPU (co-resident CTAs of a cooperative grid, shared
+    // memory per CTA, cluster residency) or an attribute query failed.
+    set_err(c, "%s: the launch exceeds this GPU's limits (co-resident CTAs, shared memory or "
+               "cluster size) for this problem size", what);
+    return FRAM_ERR_INVALID;
+  }
   set_err(c, "%s: %s", what, cudaGetErrorString(e));
   cudaGetLastError();
   return FRAM_ERR_CUDA;
@@ -737,6 +745,55 @@ fram_status fram_sdsn(fram_ctx* c, int n, const double* X, double* D, double the
   L.barrier = &w.scal->bar;
   L.limit_ns = c->wait_limit_ns;
   FR_LAUNCH(launch_sdsn_fp64(L, c->num_sms, c->stream), "sdsn kernel");
+  FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.sdsn, &w.scal->iter.sdsn, sizeof(SdsnStats),
+                          cudaMemcpyDeviceToHost, c->stream),
+          "readback");
+  FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  const SdsnStats& st = w.hscal->iter.sdsn;
+  FR_TRY(dev_status(c, st.status, "SDSN"));
+  if (sweeps_out) *sweeps_out = st.sweeps;
+  if (gamma_out) *gamma_out = st.gamma;
+  return FRAM_OK;
+}
+
+fram_status fram_sdsn_f32(fram_ctx* c, int n, const float* X, int ldx, float* D, int ldd,
+                          double theta, double gamma_tol, int max_sweeps, int* sweeps_out,
+                          double* gamma_out) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (n < 1 || ldx < n || ldd < n || !X || !D || !is_device_ptr(X) || !is_device_ptr(D) ||
+      !(theta > 0.0) || max_sweeps < 1) {
+    set_err(c, "fram_sdsn_f32: n >= 1, ldx >= n, ldd >= n, device X and D, theta > 0, "
+               "max_sweeps >= 1 are required");
+    return FRAM_ERR_INVALID;
+  }
+  if (X == D && ldx != ldd) {
+    set_err(c, "fram_sdsn_f32: in place (D == X) needs ldd == ldx");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  FR_TRY(ensure_workspace(c, n));
+  Workspace& w = c->ws;
+  FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream), "memset");
+  FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
+  FR_LAUNCH(launch_max_f32(X, ldx, n, &w.scal->xmax_key, c->stream), "max kernel");
+  SdsnLaunch L{};
+  L.n = n;
+  L.X = X;
+  L.ldx = ldx;
+  L.Y = D;
+  L.ldy = ldd;
+  L.in_fp32 = 1;
+  L.out_fp32 = 1;
+  L.theta = theta;
+  L.gamma_tol = gamma_tol;
+  L.max_sweeps = max_sweeps;
+  L.xmax_key = &w.scal->xmax_key;
+  L.stats = &w.scal->iter.sdsn;
+  L.partials = w.sdsn_partials;
+  L.barrier = &w.scal->bar;
+  L.limit_ns = c->wait_limit_ns;
+  FR_LAUNCH(launch_sdsn(L, c->num_sms, c->stream), "sdsn kernel");
   FR_CUDA(cudaMemcpyAsync(&w.hscal->iter.sdsn, &w.scal->iter.sdsn, sizeof(SdsnStats),
                           cudaMemcpyDeviceToHost, c->stream),
           "readback");

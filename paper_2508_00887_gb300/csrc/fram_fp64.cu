@@ -325,11 +325,13 @@ __global__ void __launch_bounds__(256) nt_gemm_kernel(const double* __restrict__
     }
 }
 
-__global__ void max_kernel(const double* __restrict__ X, int ldx, int n, unsigned long long* out) {
+template <typename T>
+__global__ void max_kernel(const T* __restrict__ X, int ldx, int n, unsigned long long* out) {
   __shared__ double red[kRowThreads / 32];
   double m = -INFINITY;
   for (int i = blockIdx.x; i < n; i += gridDim.x)
-    for (int j = threadIdx.x; j < n; j += kRowThreads) m = fmax(m, X[(size_t)i * ldx + j]);
+    for (int j = threadIdx.x; j < n; j += kRowThreads)
+      m = fmax(m, (double)X[(size_t)i * ldx + j]);
   const double bm = block_max<kRowThreads>(m, red);
   if (threadIdx.x == 0 && bm > -INFINITY) atomicMax(out, ordered_key(bm));
 }
@@ -380,7 +382,12 @@ int launch_node_affinity(const double* F, const double* Ft, int n, int d, double
 }
 
 int launch_max(const double* X, int ldx, int n, unsigned long long* out, cudaStream_t s) {
-  max_kernel<<<grid_rows(n), kRowThreads, 0, s>>>(X, ldx, n, out);
+  max_kernel<double><<<grid_rows(n), kRowThreads, 0, s>>>(X, ldx, n, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_max_f32(const float* X, int ldx, int n, unsigned long long* out, cudaStream_t s) {
+  max_kernel<float><<<grid_rows(n), kRowThreads, 0, s>>>(X, ldx, n, out);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

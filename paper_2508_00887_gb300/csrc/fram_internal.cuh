@@ -19,8 +19,8 @@ constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s
 // A launch fact computed once per device (a kernel attribute set, an
 // occupancy, the SM count): function attributes are per device, and several
 // contexts -- on several devices, or the serving thread beside the caller's
-// -- may ask at once.  compute() returns the value to keep; 0 means "not
-// computed" and is never kept.
+// -- may ask at once.  compute() returns the value to keep; only positive
+// values are kept, so a failed query (<= 0) is retried on the next call.
 constexpr int kMaxDevices = 64;
 
 struct DeviceCache {
@@ -33,8 +33,10 @@ int device_cached(DeviceCache& c, F compute) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
   std::lock_guard<std::mutex> lk(c.mu);
-  if (c.val[dev] == 0) c.val[dev] = compute();
-  return c.val[dev];
+  if (c.val[dev] > 0) return c.val[dev];
+  const int v = compute();
+  if (v > 0) c.val[dev] = v;
+  return v;
 }
 
 // ------------------------------------------------------------ device helpers
@@ -240,6 +242,7 @@ int launch_transpose(const double* Src, double* Dst, int ld, int n, const double
 int launch_node_affinity(const double* F, const double* Ft, int n, int d, double* K,
                          cudaStream_t s);
 int launch_max(const double* X, int ldx, int n, unsigned long long* key, cudaStream_t s);
+int launch_max_f32(const float* X, int ldx, int n, unsigned long long* key, cudaStream_t s);
 
 struct SdsnLaunch {
   int n;

@@ -66,6 +66,12 @@ void put_err(char* err, size_t len, const char* msg, const char* detail = "") {
 }
 
 fram_status cuda_err(char* err, size_t len, const char* what, cudaError_t e) {
+  if (e == cudaSuccess) {  // refused by a launch limit, not by a CUDA call
+    if (err && len)
+      snprintf(err, len, "%s: the launch exceeds this GPU's limits (co-resident CTAs or shared "
+                         "memory) for this problem size", what);
+    return FRAM_ERR_INVALID;
+  }
   if (err && len) snprintf(err, len, "%s: %s", what, cudaGetErrorString(e));
   cudaGetLastError();
   return FRAM_ERR_CUDA;

@@ -86,11 +86,22 @@ def solve(torch, ctx, g, precision, max_polish=4):
     return X.cpu().numpy(), P.cpu().numpy().astype(np.int64), info
 
 
+# Relative Frobenius distance of the mixed N from the oracle's N allowed per
+# precision: a few times the largest value measured on the workloads below
+# (n = 50 to 1000 ER pairs, n = 300 Gaussian pair).  The gradient's input
+# rounding (2^-9 relative for BF16, 2^-12 for TF32) sets its scale.
+X_TOL = {fr.FRAM_PREC_MIXED_BF16: 5e-3, fr.FRAM_PREC_MIXED_TF32: 1e-3}
+
+
 def check_equal_accuracy(g, ref, X, P, info):
+    """Equal accuracy as the metric defines it, both ways: planted-match
+    accuracy within 0.5 percentage points of the oracle's and objective within
+    1e-3 relative of the oracle's (a mixed result that drifts to a different,
+    better-scoring permutation fails too)."""
     acc_o = o.accuracy(ref.perm, g.truth)
     acc_m = o.accuracy(P, g.truth)
-    assert acc_m >= acc_o - 0.005
-    assert info.objective >= ref.objective - 1e-3 * abs(ref.objective)  # not worse
+    assert abs(acc_m - acc_o) <= 0.005
+    assert abs(info.objective - ref.objective) <= 1e-3 * abs(ref.objective)
     assert sorted(P.tolist()) == list(range(g.n))
     # the objective the kernels report is the one of the returned permutation
     assert abs(info.objective - o.objective(g.A, g.B, P)) <= 1e-9 * abs(info.objective)
@@ -104,7 +115,8 @@ def test_mixed_small_er_equal_accuracy(torch_cuda, ctx, precision, seed):
     ref = o.fram(g.A, g.B, theta=g.theta)
     X, P, info = solve(torch_cuda, ctx, g, precision)
     err = check_equal_accuracy(g, ref, X, P, info)
-    assert err < 0.05
+    print(f"n={g.n} precision={precision} relF(N)={err:.3e}")
+    assert err <= X_TOL[precision]
     assert info.total_sweeps > 0 and info.outer_iters >= 1
 
 
@@ -116,14 +128,16 @@ def test_mixed_medium_equal_accuracy(torch_cuda, ctx, precision):
     err = check_equal_accuracy(g, ref, X, P, info)
     print(f"precision={precision} relF(N)={err:.3e} outer={info.outer_iters} "
           f"sweeps={info.total_sweeps} polish={info.polish_sweeps}")
-    assert err < 0.05
+    assert err <= X_TOL[precision]
 
 
 def test_mixed_dense_gaussian_equal_accuracy(torch_cuda, ctx):
     g = fi.gaussian_pair(300, jitter=0.01, seed=2)
     ref = o.fram(g.A, g.B, theta=g.theta)
     X, P, info = solve(torch_cuda, ctx, g, fr.FRAM_PREC_MIXED_BF16)
-    check_equal_accuracy(g, ref, X, P, info)
+    err = check_equal_accuracy(g, ref, X, P, info)
+    print(f"gaussian n={g.n} relF(N)={err:.3e}")
+    assert err <= X_TOL[fr.FRAM_PREC_MIXED_BF16]
 
 
 def test_mixed_polish_reaches_fp64_tolerance(torch_cuda, ctx):
@@ -169,3 +183,63 @@ def test_mixed_stops_at_rounding_floor(torch_cuda, ctx):
     p.stall_ratio = 0.0
     _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
     assert info.outer_iters == 60
+
+
+def test_fp64_streaming_sizes_match_oracle(torch_cuda, ctx):
+    # n = 2800: SDSN tiles of 234 x 236 (FP64 or FP32) exceed shared memory and
+    # stream through L2 each sweep.  Two outer iterations of 50 sweeps of the
+    # FP64 path against the oracle at the parity tolerance; the full mixed
+    # solves of the same pair are compared with this path below.
+    torch = torch_cuda
+    g = fi.er_pair(2800, 0.05, noise=0.05, flip_frac=0.05, seed=3)
+    ref = o.fram(g.A, g.B, theta=g.theta, max_outer=2, max_sweeps=50)
+    n = g.n
+    X = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    P = torch.empty(n, dtype=torch.int32, device="cuda")
+    p64 = fr.fram_default_params(theta=g.theta, max_outer=2, max_sweeps=50)
+    _, info = fr.fram_solve(ctx, n, torch.from_numpy(g.A).cuda(), torch.from_numpy(g.B).cuda(),
+                            None, p64, X, P)
+    assert relF(X.cpu().numpy(), ref.N) <= 1e-9
+    assert info.total_sweeps == ref.total_sweeps and info.outer_iters == 2
+    assert abs(info.delta - ref.delta) <= 1e-9 * ref.delta
+
+
+_FP64_SOLVES = {}
+
+
+def fp64_solve(torch, ctx, n, seed):
+    """An ER pair (p = 0.05, noise 0.05, 5% flips, theta = 10) of size n solved
+    by the GPU FP64 path (which matches the oracle at the parity tolerance)."""
+    if n not in _FP64_SOLVES:
+        g = fi.er_pair(n, 0.05, noise=0.05, flip_frac=0.05, seed=seed)
+        A = torch.from_numpy(g.A).cuda()
+        B = torch.from_numpy(g.B).cuda()
+        X = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        P = torch.empty(n, dtype=torch.int32, device="cuda")
+        _, info = fr.fram_solve(ctx, n, A, B, None, fr.fram_default_params(theta=g.theta), X, P)
+        _FP64_SOLVES[n] = (g, A, B, X.cpu().numpy(), P.cpu().numpy().astype(np.int64), info)
+    return _FP64_SOLVES[n]
+
+
+@pytest.mark.parametrize("precision", [fr.FRAM_PREC_MIXED_BF16, fr.FRAM_PREC_MIXED_TF32])
+@pytest.mark.parametrize("n,seed", [(2800, 3), (4096, 4)])
+def test_mixed_full_solve_streaming_equal_accuracy(torch_cuda, ctx, precision, n, seed):
+    # Full mixed solves where the FP32 SDSN streams its tiles through L2 (n =
+    # 2800: two 16-byte groups per lane; n = 4096: six) against the FP64 solve
+    # of the same pair: equal accuracy both ways and N within the precision's
+    # tolerance.
+    torch = torch_cuda
+    g, A, B, N64, P64, i64 = fp64_solve(torch, ctx, n, seed)
+    X = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    P = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = fr.fram_default_params(theta=g.theta, precision=precision, max_polish=4)
+    _, info = fr.fram_solve(ctx, n, A, B, None, p, X, P)
+    Pm = P.cpu().numpy().astype(np.int64)
+    err = relF(X.cpu().numpy(), N64)
+    acc_m, acc_64 = o.accuracy(Pm, g.truth), o.accuracy(P64, g.truth)
+    print(f"n={n} precision={precision} relF(N)={err:.3e} acc={acc_m:.4f}/{acc_64:.4f} "
+          f"obj={info.objective:.6f}/{i64.objective:.6f} outer={info.outer_iters}/{i64.outer_iters}")
+    assert sorted(Pm.tolist()) == list(range(n))
+    assert abs(acc_m - acc_64) <= 0.005
+    assert abs(info.objective - i64.objective) <= 1e-3 * abs(i64.objective)
+    assert err <= X_TOL[precision]
