@@ -270,6 +270,15 @@ int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned lo
                double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
                SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
+// FP32 SDSN of one problem in one thread-block cluster (96 < n <= 1024, mode
+// 0, no gate): 1 launched, 0 not applicable (use the grid form), -1 error.
+int launch_sdsn_cluster(const SdsnLaunch& L, cudaStream_t s);
+// Cluster class of a problem (0: the cluster form does not apply); problems
+// of one class can share one grouped launch, each on its own cluster.
+int sdsn_cluster_class(const SdsnLaunch& L);
+int launch_sdsn_cluster_group(const SdsnLaunch* L, int count, void* ddesc, size_t ddesc_bytes,
+                              cudaStream_t s);
+size_t sdsn_cluster_desc_bytes();
 int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 // Several problems (same precision pair) in one cooperative launch of at most
 // max_blocks CTAs; ddesc is device scratch of sdsn_group_desc_bytes(count).

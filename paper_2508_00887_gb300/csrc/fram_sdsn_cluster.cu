@@ -1,0 +1,688 @@
+// SDSN (Alg. 2 of arXiv 2508.00887) in FP32 for 96 < n <= 1024, held
+// entirely on chip by ONE thread-block cluster of s x s CTAs (s = 1, 2 or 4;
+// 16 CTAs is a non-portable cluster size).
+//
+//   step 1   Y = (theta/2) X / max(X)
+//   sweep    Y_ij <- max(0, Y_ij + 1/n + S/n^2 - r_i/n - c_j/n)      (eq. 7)
+//   stop     gamma = sum(Y)/n - 1 <= gamma_tol, or max_sweeps sweeps
+//
+// Why a cluster: one sweep needs the row sums, column sums and total of the
+// previous sweep, a global all-reduce.  Among co-resident CTAs of a grid that
+// reduction goes through L2 -- a store becomes visible to another SM after
+// about 0.37 us, and among 144 CTAs the exchange costs about 3 us per sweep,
+// more than the sweep's arithmetic.  Within a cluster the partial sums are
+// read from the other CTAs' shared memory (DSMEM) after one hardware cluster
+// barrier (about 0.3 us), so no sweep touches global memory at all.
+//
+// Layout: CTA (bi, bj) of the s x s cluster owns the tr x tc tile at rows
+// bi*tr, columns bj*tc (tc a multiple of 4).  16 warps; warp w owns tile
+// rows w, w+16, w+32, ...; lane l owns the 16-byte column groups l and l+32
+// (G = 2, tc <= 256) or l (G = 1).  The first RR rows of each warp are held
+// in registers, the remaining ones in shared memory.  Padding columns carry
+// b_j = +inf, so every sweep leaves them at 0 without a test per element.
+//
+// Per sweep: the pass updates the tile and accumulates per-lane row and
+// column sums; row sums are reduced across each warp by a transposing
+// shuffle tree, column sums across warps through shared memory, the tile
+// total from the warps' row sums.  The three are published in the CTA's own
+// shared memory (double-buffered by sweep parity), one cluster barrier makes
+// them visible, and every CTA gathers the partials of its rows (from the s
+// CTAs of its tile row), of its columns (s CTAs of its tile column) and all
+// s*s totals, in a fixed order: every CTA forms the same S and gamma, so all
+// of them stop at the same sweep and execute the same cluster barriers.
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fram_internal.cuh"
+
+namespace fram {
+
+namespace {
+
+constexpr int kCT = 512;           // threads per CTA
+constexpr int kCW = kCT / 32;      // warps per CTA
+constexpr int kMaxTile = 256;      // tr, tc <= 256
+constexpr int kMaxRowsPerWarp = kMaxTile / kCW;  // 16
+
+struct ClusterK {
+  int n, s, tr, tc;
+  int vec_x, vec_y;
+  const float* X;
+  int ldx;
+  float* Y;
+  int ldy;
+  double theta, gamma_tol;
+  int max_sweeps;
+  const unsigned long long* xmax_key;
+  SdsnStats* stats;
+};
+
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared-memory layout (floats unless noted), fixed for a kernel variant.
+// Tiles are padded to TCP = 128 G columns and kMaxTile rows: every lane owns
+// G whole 16-byte groups and every warp 16 rows, so the sweep loop has no
+// bounds tests.  Padding rows carry a_i = -inf and padding columns b_j =
+// +inf; their entries therefore stay 0 and add nothing to any sum.
+//   ts      [kCW * RS][TCP]   tile rows held in shared memory (RS = 16 - RR)
+//   colacc  [kCW][TCP]        per-warp column sums
+//   arow    [kMaxTile]        1/n - r_i/n (-inf on padding rows)
+//   bcol    [TCP]             c_j/n (+inf on padding columns)
+//   rpub    [2][kMaxTile]     published row partials (by sweep parity)
+//   cpub    [2][TCP]          published column partials
+//   wtot    [kCW]             per-warp totals
+//   tpub    [2]               published tile totals
+template <int G, int RR>
+struct SmemLayout {
+  static constexpr int TCP = 128 * G;
+  static constexpr int RS = kMaxRowsPerWarp - RR;
+  static constexpr size_t ts = 0;
+  static constexpr size_t colacc = ts + (size_t)kCW * RS * TCP * 4;
+  static constexpr size_t arow = colacc + (size_t)kCW * TCP * 4;
+  static constexpr size_t bcol = arow + (size_t)kMaxTile * 4;
+  static constexpr size_t rpub = bcol + (size_t)TCP * 4;
+  static constexpr size_t cpub = rpub + (size_t)2 * kMaxTile * 4;
+  static constexpr size_t wtot = cpub + (size_t)2 * TCP * 4;
+  static constexpr size_t tpub = wtot + (size_t)kCW * 4;
+  static constexpr size_t bytes = tpub + 2 * 4;
+};
+
+// Two FP32 values in one 64-bit register (low word = lower address), and the
+// packed FP32x2 arithmetic of sm_100+ (each lane of the pair rounded to
+// nearest, exactly as two scalar operations): half the instructions per
+// element, which bounds a sweep on the 16 SMs of one cluster.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t pack2(float lo, float hi) {
+  f2_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void unpack2(f2_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// max(0, .) of both halves (P2 of eq. 7).
+__device__ __forceinline__ f2_t relu2(f2_t v) {
+  float lo, hi;
+  unpack2(v, lo, hi);
+  return pack2(fmaxf(lo, 0.f), fmaxf(hi, 0.f));
+}
+// The sweep of eq. 7 on one pair: max(0, (y + a) - b), then both sums.
+__device__ __forceinline__ f2_t sweep2(f2_t y, f2_t aa, f2_t bb, f2_t& racc, f2_t& cacc) {
+  const f2_t t = relu2(sub2(add2(y, aa), bb));
+  racc = add2(racc, t);
+  cacc = add2(cacc, t);
+  return t;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::
+          : "memory");
+}
+
+// Address of the same shared-memory word in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t remote(const void* local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ float ld_remote_f32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ double ld_remote_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Sum of v[0..15] over the 32 lanes of a warp, transposed: afterwards lane l
+// holds the total of entry ((l >> 4) & 1) * 8 + ((l >> 3) & 1) * 4 +
+// ((l >> 2) & 1) * 2 + ((l >> 1) & 1), and lanes l, l ^ 1 hold the same one.
+// 16 shuffles instead of 80; the addition order is fixed.
+__device__ __forceinline__ float transpose_reduce16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[m] : v[m + 8];
+    const float keep = hi ? v[m + 8] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[m] : v[m + 4];
+    const float keep = hi ? v[m + 4] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[m] : v[m + 2];
+    const float keep = hi ? v[m + 2] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ int transpose_index16(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+template <int G, int RR>
+__device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned char* smem) {
+  using Lay = SmemLayout<G, RR>;
+  constexpr int TCP = Lay::TCP;
+  constexpr int RS = Lay::RS;
+  __shared__ float s_S[2];  // S of the last gathered sweep as hi + lo (double-float)
+  __shared__ float s_cS;    // S / n^2 for the next sweep
+  __shared__ int s_stop;
+  float* ts = reinterpret_cast<float*>(smem + Lay::ts);
+  float* colacc = reinterpret_cast<float*>(smem + Lay::colacc);
+  float* arow = reinterpret_cast<float*>(smem + Lay::arow);
+  float* bcol = reinterpret_cast<float*>(smem + Lay::bcol);
+  float* rpub = reinterpret_cast<float*>(smem + Lay::rpub);
+  float* cpub = reinterpret_cast<float*>(smem + Lay::cpub);
+  float* wtot = reinterpret_cast<float*>(smem + Lay::wtot);
+  float* tpub = reinterpret_cast<float*>(smem + Lay::tpub);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int s = p.s;
+  const uint32_t rank = s > 1 ? cluster_rank() : 0u;
+  const int bi = (int)rank / s, bj = (int)rank % s;
+  const int r0 = bi * p.tr, c0 = bj * p.tc;
+  const int nr = max(0, min(p.tr, p.n - r0)), nc = max(0, min(p.tc, p.n - c0));
+
+  // Alg. 2 step 1.  Every CTA reads the same max, so a degenerate input makes
+  // all of them return before the first cluster barrier.
+  const double m = from_ordered_key(*p.xmax_key);
+  if (!(m > 0.0)) {
+    if (rank == 0 && tid == 0) {
+      p.stats->status = DEV_DEGENERATE;
+      p.stats->sweeps = 0;
+      p.stats->converged = 0;
+      p.stats->gamma = INFINITY;
+      p.stats->xmax = m;
+    }
+    return;
+  }
+  const double n_d = (double)p.n;
+  const double inv_n = 1.0 / n_d, inv_n2 = inv_n * inv_n;
+  const float inv_n_f = (float)inv_n, inv_n2_f = (float)inv_n2;
+  const float scale = (float)((p.theta / 2.0) / m);
+  // The stop test gamma = S/n - 1 <= gamma_tol, as S <= n (1 + gamma_tol),
+  // with the threshold as a double-float; FP64 work stays out of the sweep
+  // loop (FP64 instructions are scarce on this GPU).
+  const double thr = n_d * (1.0 + p.gamma_tol);
+  const float thr_hi = (float)thr, thr_lo = (float)(thr - (double)thr_hi);
+  const f2_t zero2 = pack2(0.f, 0.f);
+  const f2_t scale2 = pack2(scale, scale);
+
+  // Padding terms, written once: gathers only ever write valid rows/columns.
+  for (int i = nr + tid; i < kMaxTile; i += kCT) arow[i] = -INFINITY;
+  for (int j = nc + tid; j < TCP; j += kCT) bcol[j] = INFINITY;
+
+  f2_t y[RR][G][2];  // register rows: column pairs (j0, j0 + 1), (j0 + 2, j0 + 3)
+  float racc[16];    // per-lane row sums
+  f2_t cacc2[G][2];  // per-lane column sums
+  float cS = 0.f;
+
+  // Alg. 2 step 1 for one 16-byte group: (theta/2) X / max X, 0 outside the tile.
+  auto load_x = [&](int i, int j0, f2_t& a, f2_t& b) {
+    if (i >= nr) {
+      a = b = zero2;
+      return;
+    }
+    const float* xr = p.X + (size_t)(r0 + i) * p.ldx + c0 + j0;
+    if (p.vec_x && j0 + 4 <= nc) {
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(xr);
+      a = mul2(x.x, scale2);
+      b = mul2(x.y, scale2);
+    } else {
+      float t[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) t[v] = j0 + v < nc ? xr[v] * scale : 0.f;
+      a = pack2(t[0], t[1]);
+      b = pack2(t[2], t[3]);
+    }
+  };
+
+  auto first_pass = [&]() {
+#pragma unroll
+    for (int g = 0; g < G; ++g) cacc2[g][0] = cacc2[g][1] = zero2;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = warp + kCW * r;
+      f2_t rp = zero2;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int j0 = 4 * (lane + 32 * g);
+        f2_t t[2];
+        load_x(i, j0, t[0], t[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          rp = add2(rp, t[h]);
+          cacc2[g][h] = add2(cacc2[g][h], t[h]);
+          if (r < RR) y[r < RR ? r : 0][g][h] = t[h];
+        }
+        if (r >= RR)
+          *reinterpret_cast<ulonglong2*>(ts + (size_t)(warp + kCW * (r - RR)) * TCP + j0) =
+              make_ulonglong2(t[0], t[1]);
+      }
+      float lo, hi;
+      unpack2(rp, lo, hi);
+      racc[r] = lo + hi;
+    }
+  };
+
+  // The fused P1 + P2 sweep (eq. 7) over the tile; no bounds tests.
+  auto sweep_pass = [&]() {
+#pragma unroll
+    for (int g = 0; g < G; ++g) cacc2[g][0] = cacc2[g][1] = zero2;
+    f2_t bb[G][2];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(bcol + 4 * (lane + 32 * g));
+      bb[g][0] = b.x;
+      bb[g][1] = b.y;
+    }
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const float ai = arow[warp + kCW * r] + cS;
+      const f2_t aa = pack2(ai, ai);
+      f2_t rp = zero2;
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) y[r][g][h] = sweep2(y[r][g][h], aa, bb[g][h], rp, cacc2[g][h]);
+      float lo, hi;
+      unpack2(rp, lo, hi);
+      racc[r] = lo + hi;
+    }
+    if constexpr (RS > 0) {
+      // Shared-memory rows, software-pipelined: the next row's groups are
+      // loaded before the current row is stored.
+      const float* base = ts + (size_t)warp * TCP + 4 * lane;
+      ulonglong2 cur[G], nxt[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) cur[g] = *reinterpret_cast<const ulonglong2*>(base + 128 * g);
+#pragma unroll
+      for (int q = 0; q < RS; ++q) {
+        float* row = ts + (size_t)(warp + kCW * q) * TCP + 4 * lane;
+        if (q + 1 < RS) {
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            nxt[g] = *reinterpret_cast<const ulonglong2*>(row + (size_t)kCW * TCP + 128 * g);
+        }
+        const float ai = arow[warp + kCW * (RR + q)] + cS;
+        const f2_t aa = pack2(ai, ai);
+        f2_t rp = zero2;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const f2_t t0 = sweep2(cur[g].x, aa, bb[g][0], rp, cacc2[g][0]);
+          const f2_t t1 = sweep2(cur[g].y, aa, bb[g][1], rp, cacc2[g][1]);
+          *reinterpret_cast<ulonglong2*>(row + 128 * g) = make_ulonglong2(t0, t1);
+        }
+        float lo, hi;
+        unpack2(rp, lo, hi);
+        racc[RR + q] = lo + hi;
+#pragma unroll
+        for (int g = 0; g < G; ++g) cur[g] = nxt[g];
+      }
+    }
+  };
+
+  // Reduce the pass's sums and publish them into parity buffer `par`.
+  auto publish = [&](const int par) {
+    const float rs = transpose_reduce16(racc, lane);
+    const int ri = warp + kCW * transpose_index16(lane);
+    const bool holder = (lane & 1) == 0 && ri < nr;
+    if (holder) rpub[par * kMaxTile + ri] = rs;
+    const float wt = warp_sum(holder ? rs : 0.f);
+    if (lane == 0) wtot[warp] = wt;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      *reinterpret_cast<ulonglong2*>(colacc + warp * TCP + 4 * (lane + 32 * g)) =
+          make_ulonglong2(cacc2[g][0], cacc2[g][1]);
+    __syncthreads();
+    if (tid < TCP) {
+      float c = 0.f;
+#pragma unroll
+      for (int w = 0; w < kCW; ++w) c += colacc[w * TCP + tid];
+      cpub[par * TCP + tid] = c;
+    } else if (tid == TCP || (TCP == kCT && tid == 0)) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < kCW; ++w) t += wtot[w];
+      tpub[par] = t;
+    }
+  };
+
+  // After the cluster barrier: warp 0 forms S (FP64, from the s*s tile
+  // totals), gamma, S/n^2 and the stop test; the other 15 warps form the
+  // next sweep's row and column terms from the partials of their rows and
+  // columns, each summed over the s CTAs in a fixed order.
+  auto gather = [&](const int par, const int k) {
+    if (warp == 0) {
+      // S: the s*s tile totals summed in a fixed order as a double-float
+      // (TwoSum: exact up to the final hi + lo rounding, ~2^-48 relative).
+      float t = 0.f;
+      if (lane < s * s) t = s > 1 ? ld_remote_f32(remote(&tpub[par], (uint32_t)lane)) : tpub[par];
+      float hi = 0.f, lo = 0.f;
+      for (int q = 0; q < s * s; ++q) {
+        const float tq = __shfl_sync(0xffffffffu, t, q);
+        float e;
+        two_sum(hi, tq, hi, e);
+        lo += e;
+      }
+      {
+        float e;
+        two_sum(hi, lo, hi, e);
+        lo = e;
+      }
+      if (lane == 0) {
+        s_S[0] = hi;
+        s_S[1] = lo;
+        s_cS = hi * inv_n2_f + lo * inv_n2_f;
+        const bool below = hi < thr_hi || (hi == thr_hi && lo <= thr_lo);
+        s_stop = (k > 0 && below) ? 1 : 0;
+      }
+      return;
+    }
+    // Up to two entries per thread (nr + nc <= 512, 480 threads).
+    int es[2] = {tid - 32, tid - 32 + (kCT - 32)};
+    float v[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = es[u];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[u][q] = 0.f;
+      if (e < nr) {
+        const float* loc = &rpub[par * kMaxTile + e];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < s) v[u][q] = s > 1 ? ld_remote_f32(remote(loc, (uint32_t)(bi * s + q))) : *loc;
+      } else if (e < nr + nc) {
+        const float* loc = &cpub[par * TCP + (e - nr)];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < s) v[u][q] = s > 1 ? ld_remote_f32(remote(loc, (uint32_t)(q * s + bj))) : *loc;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = es[u];
+      const float acc = ((v[u][0] + v[u][1]) + v[u][2]) + v[u][3];
+      if (e < nr)
+        arow[e] = inv_n_f - acc * inv_n_f;
+      else if (e < nr + nc)
+        bcol[e - nr] = acc * inv_n_f;
+    }
+  };
+
+  first_pass();
+  publish(0);
+  if (s > 1) cluster_sync(); else __syncthreads();
+  gather(0, 0);
+  __syncthreads();
+  int k = 0;
+  while (true) {
+    if (s_stop || k >= p.max_sweeps) break;
+    cS = s_cS;
+    sweep_pass();
+    ++k;
+    publish(k & 1);
+    if (s > 1) cluster_sync(); else __syncthreads();
+    gather(k & 1, k);
+    __syncthreads();
+  }
+  // No CTA may leave while another can still read its shared memory.
+  if (s > 1) cluster_sync();
+
+  // Store the tile.
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = warp + kCW * r;
+    if (i >= nr) continue;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int j0 = 4 * (lane + 32 * g);
+      if (j0 >= nc) continue;
+      ulonglong2 t;
+      if (r < RR) {
+        t.x = y[r < RR ? r : 0][g][0];
+        t.y = y[r < RR ? r : 0][g][1];
+      } else {
+        t = *reinterpret_cast<const ulonglong2*>(ts + (size_t)(warp + kCW * (r - RR)) * TCP + j0);
+      }
+      float* yr = p.Y + (size_t)(r0 + i) * p.ldy + c0 + j0;
+      if (p.vec_y && j0 + 4 <= nc) {
+        *reinterpret_cast<ulonglong2*>(yr) = t;
+      } else {
+        float f[4];
+        unpack2(t.x, f[0], f[1]);
+        unpack2(t.y, f[2], f[3]);
+#pragma unroll
+        for (int vv = 0; vv < 4; ++vv)
+          if (j0 + vv < nc) yr[vv] = f[vv];
+      }
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    const double g = k > 0 ? ((double)s_S[0] + (double)s_S[1]) * inv_n - 1.0 : INFINITY;
+    p.stats->sweeps = k;
+    p.stats->gamma = g;
+    p.stats->converged = (g <= p.gamma_tol) ? 1 : 0;
+    p.stats->xmax = m;
+  }
+}
+
+template <int G, int RR>
+__global__ void __launch_bounds__(kCT, 1) sdsn_cluster_kernel(const __grid_constant__ ClusterK p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  sdsn_cluster_body<G, RR>(p, smem);
+}
+
+// Many independent problems of one cluster shape in one launch: cluster c
+// solves problem c.  Clusters never wait on one another, so the launch needs
+// no co-residency and any number of problems fit.
+template <int G, int RR>
+__global__ void __launch_bounds__(kCT, 1) sdsn_cluster_group_kernel(const ClusterK* probs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  // By reference: fields are read from the descriptor array where used
+  // instead of occupying registers for the whole launch.
+  const ClusterK& p = probs[blockIdx.x / (unsigned)(probs[0].s * probs[0].s)];
+  sdsn_cluster_body<G, RR>(p, smem);
+}
+
+// Cluster side s for n: one CTA up to 256, 2 x 2 up to 512, 4 x 4 up to 1024.
+int cluster_side(int n) { return n <= 256 ? 1 : n <= 512 ? 2 : 4; }
+
+// Fill the problem descriptor; false when this form does not apply.
+bool make_cluster_problem(const SdsnLaunch& L, ClusterK& k) {
+  if (!L.in_fp32 || !L.out_fp32 || L.mode != 0 || L.gate != nullptr) return false;
+  if (L.n <= 96 || L.n > 1024) return false;
+  k = ClusterK{};
+  k.n = L.n;
+  k.s = cluster_side(L.n);
+  k.tr = (L.n + k.s - 1) / k.s;
+  k.tc = (k.tr + 3) / 4 * 4;
+  if (k.tr > kMaxTile || k.tc > kMaxTile) return false;
+  k.X = static_cast<const float*>(L.X);
+  k.ldx = L.ldx;
+  k.Y = static_cast<float*>(L.Y);
+  k.ldy = L.ldy;
+  k.vec_x = (reinterpret_cast<uintptr_t>(k.X) % 16 == 0) && (k.ldx % 4 == 0);
+  k.vec_y = (reinterpret_cast<uintptr_t>(k.Y) % 16 == 0) && (k.ldy % 4 == 0);
+  k.theta = L.theta;
+  k.gamma_tol = L.gamma_tol;
+  k.max_sweeps = L.max_sweeps;
+  k.xmax_key = L.xmax_key;
+  k.stats = L.stats;
+  return true;
+}
+
+// Kernel attributes set, and a cluster of s*s CTAs with `smem` bytes each
+// schedulable on this GPU (checked once per shape and device).
+template <int G, int RR>
+bool cluster_ready(int s, size_t smem) {
+  static DeviceCache attr;
+  if (device_cached(attr, [] {
+        const void* f1 = (const void*)sdsn_cluster_kernel<G, RR>;
+        const void* f2 = (const void*)sdsn_cluster_group_kernel<G, RR>;
+        for (const void* f : {f1, f2}) {
+          if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+                  cudaSuccess ||
+              cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                  cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+          }
+        }
+        return 1;
+      }) < 0)
+    return false;
+  static DeviceCache fits[3];
+  const int si = s == 1 ? 0 : s == 2 ? 1 : 2;
+  return device_cached(fits[si], [&] {
+           cudaLaunchConfig_t cfg = {};
+           cfg.gridDim = dim3((unsigned)(s * s));
+           cfg.blockDim = dim3(kCT);
+           cfg.dynamicSmemBytes = 200 * 1024;
+           cudaLaunchAttribute at[1];
+           at[0].id = cudaLaunchAttributeClusterDimension;
+           at[0].val.clusterDim.x = (unsigned)(s * s);
+           at[0].val.clusterDim.y = 1;
+           at[0].val.clusterDim.z = 1;
+           cfg.attrs = at;
+           cfg.numAttrs = 1;
+           int ncl = 0;
+           if (cudaOccupancyMaxActiveClusters(&ncl, sdsn_cluster_kernel<G, RR>, &cfg) !=
+               cudaSuccess) {
+             cudaGetLastError();
+             return -1;
+           }
+           return ncl > 0 ? 1 : -1;
+         }) > 0 &&
+         smem <= 200 * 1024;
+}
+
+template <int G, int RR>
+int launch_cluster_t(const ClusterK* dk, const ClusterK* hk, int count, size_t smem,
+                     cudaStream_t st) {
+  const int s = hk[0].s;
+  if (!cluster_ready<G, RR>(s, smem)) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(count * s * s));
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)(s * s);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = dk == nullptr ? cudaLaunchKernelEx(&cfg, sdsn_cluster_kernel<G, RR>, hk[0])
+                                : cudaLaunchKernelEx(&cfg, sdsn_cluster_group_kernel<G, RR>, dk);
+  return e == cudaSuccess ? 1 : -1;
+}
+
+size_t problem_smem(const ClusterK& k) {
+  return k.tc <= 128 ? SmemLayout<1, 16>::bytes : SmemLayout<2, 8>::bytes;
+}
+
+}  // namespace
+
+// FP32 SDSN of one problem in one cluster.  Returns 1 when launched, 0 when
+// this form does not apply (size, shape, or the cluster is not schedulable:
+// the caller then uses the grid form), -1 on a launch error.
+int launch_sdsn_cluster(const SdsnLaunch& L, cudaStream_t st) {
+  ClusterK k;
+  if (!make_cluster_problem(L, k)) return 0;
+  const size_t smem = problem_smem(k);
+  if (k.tc <= 128) return launch_cluster_t<1, 16>(nullptr, &k, 1, smem, st);
+  return launch_cluster_t<2, 8>(nullptr, &k, 1, smem, st);
+}
+
+// Cluster class of a problem (problems of one class can share a grouped
+// launch): 1 + 3 * (wide tile) + (side index), 0 if the cluster form does
+// not apply.
+int sdsn_cluster_class(const SdsnLaunch& L) {
+  ClusterK k;
+  if (!make_cluster_problem(L, k)) return 0;
+  const int si = k.s == 1 ? 0 : k.s == 2 ? 1 : 2;
+  return 1 + 3 * (k.tc > 128 ? 1 : 0) + si;
+}
+
+// `count` problems of one cluster class in one launch (cluster c = problem c,
+// each computing exactly what launch_sdsn_cluster computes for it).
+// ddesc: device scratch of count * sdsn_cluster_desc_bytes().
+int launch_sdsn_cluster_group(const SdsnLaunch* L, int count, void* ddesc, size_t ddesc_bytes,
+                              cudaStream_t st) {
+  if (count < 1) return 0;
+  std::vector<ClusterK> ks(count);
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!make_cluster_problem(L[i], ks[i])) return -1;
+    if (ks[i].s != ks[0].s || (ks[i].tc > 128) != (ks[0].tc > 128)) return -1;
+    const size_t b = problem_smem(ks[i]);
+    smem = b > smem ? b : smem;
+  }
+  if (count * sizeof(ClusterK) > ddesc_bytes) return -1;
+  if (cudaMemcpyAsync(ddesc, ks.data(), count * sizeof(ClusterK), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return -1;
+  const ClusterK* dk = static_cast<const ClusterK*>(ddesc);
+  const int r = ks[0].tc <= 128 ? launch_cluster_t<1, 16>(dk, ks.data(), count, smem, st)
+                                : launch_cluster_t<2, 8>(dk, ks.data(), count, smem, st);
+  return r == 0 ? -1 : r;
+}
+
+size_t sdsn_cluster_desc_bytes() { return sizeof(ClusterK); }
+
+}  // namespace fram

@@ -354,7 +354,20 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       }
     };
     waves(L64);
-    waves(L32);
+    // FP32 problems of 96 < n <= 1024 run on one cluster each, as fram_solve
+    // runs them: one launch per cluster class, any number of problems.
+    {
+      std::vector<SdsnLaunch> grid32, cls[7];
+      for (const SdsnLaunch& L : L32) {
+        const int k = sdsn_cluster_class(L);
+        (k > 0 ? cls[k] : grid32).push_back(L);
+      }
+      for (int k = 1; k < 7 && ok; ++k)
+        if (!cls[k].empty())
+          ok = SV_OK(launch_sdsn_cluster_group(cls[k].data(), (int)cls[k].size(), S.ddesc, dbytes,
+                                               s)) && ok;
+      waves(grid32);
+    }
     waves(Lpol);
     for (Request* r : act) {
       SlotStats* st = &S.dstats[r->sid];

@@ -163,9 +163,10 @@ def test_mixed_polish_reaches_fp64_tolerance(torch_cuda, ctx):
 
 def test_mixed_stops_at_rounding_floor(torch_cuda, ctx):
     # BF16 gradients put a floor under delta (about 1e-4 at n = 1000), far
-    # above delta_tol = 1e-6: the mixed paths stop at mixed_delta_tol; with it
-    # disabled the stall safeguard stops the loop once delta stops contracting;
-    # with both disabled the loop runs to the cap.
+    # above delta_tol = 1e-6: the mixed paths stop at mixed_delta_tol or, if
+    # delta stalls just above it, by the stall safeguard; with
+    # mixed_delta_tol disabled the safeguard stops the loop once delta stops
+    # contracting; with both disabled the loop runs to the cap.
     torch = torch_cuda
     g = fi.medium_er_pair(0)
     n = g.n
@@ -175,7 +176,9 @@ def test_mixed_stops_at_rounding_floor(torch_cuda, ctx):
     p = fr.fram_default_params(theta=g.theta, precision=fr.FRAM_PREC_MIXED_BF16, max_polish=4,
                                max_outer=60)
     _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
-    assert info.outer_iters < 20 and info.delta <= p.mixed_delta_tol
+    # stopped by one of the two floor rules of reading (ix), long before the cap
+    assert info.outer_iters < 20
+    assert info.delta <= p.mixed_delta_tol or info.delta <= p.stall_below
     assert o.accuracy(P.cpu().numpy(), g.truth) == 1.0
     p.mixed_delta_tol = 0.0
     _, info = fr.fram_solve(ctx, n, A, B, None, p, None, P)
