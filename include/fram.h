@@ -208,6 +208,11 @@ fram_status fram_submit(fram_ctx *ctx, int n, const double *A, const double *B,
 fram_status fram_poll(fram_ctx *ctx, uint64_t ticket, double *X_out, int32_t *perm_out,
                       fram_info *info, int wait_ms);
 
+/* Number of scheduler ticks the context's serving loop has run (one tick =
+ * one outer iteration of every admitted request); 0 before the first
+ * fram_submit.  With fram_kernel_launches it gives the launches per tick. */
+uint64_t fram_serve_ticks(const fram_ctx *ctx);
+
 /* ---------------------------------------------------- step-level entry points
  * Single steps of the path on DEVICE buffers, for testing and composition. */
 

@@ -92,6 +92,7 @@ def load(path: str | None = None):
                                    C.POINTER(FramInfo)]),
         "fram_submit": (i, [_P, i, _P, _P, C.POINTER(FramParams), C.POINTER(u64)]),
         "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
+        "fram_serve_ticks": (u64, [_P]),
         "fram_gradient": (i, [_P, i, _P, _P, _P, _P, d, _P]),
         "fram_node_affinity": (i, [_P, i, i, _P, _P, _P]),
         "fram_fra_exact": (i, [_P, i, _P, _P, d, d, i, C.POINTER(i), C.POINTER(d)]),
@@ -117,7 +118,7 @@ def exported_symbols():
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
             "fram_solve", "fram_solve_batched", "fram_submit",
-            "fram_poll", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_f32", "fram_sdsn_grouped",
+            "fram_poll", "fram_serve_ticks", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_f32", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
 
@@ -237,6 +238,10 @@ def fram_poll(ctx, ticket, X_out=None, perm_out=None, wait_ms=0, check=True):
     if check:
         _check(ctx, st)
     return st, info
+
+
+def fram_serve_ticks(ctx) -> int:
+    return int(load().fram_serve_ticks(ctx))
 
 
 def fram_node_affinity(ctx, n, d, F, Ft, K, check=True):

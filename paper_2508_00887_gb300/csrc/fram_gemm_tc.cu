@@ -385,6 +385,223 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- grouped
+// Many independent problems in ONE persistent launch (serving: every active
+// request's gradient GEMM of a step).  Problem q has its own tensor maps, C,
+// ld, n and max key; its 128 x 128 tiles occupy global tile indices
+// [tile0_q, tile0_q + tiles_q), each in the grouped order a solo launch of
+// that problem uses, and every tile is computed exactly as the solo launch
+// computes it (same k order, same epilogue), so results do not depend on
+// which other problems share the launch.
+template <int KIND>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    gemm_tc_group_kernel(const GemmGroupProblem* __restrict__ probs, int nprob, int ntiles,
+                         int out_kind, uint64_t limit_ns) {
+  constexpr int BN = 128;
+  using C = Cfg<BN>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* smem = smem_raw + ((1024 - (raw & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * STAGES;
+  const uint32_t accf0 = empty0 + 8 * STAGES, acce0 = accf0 + 16, drain = acce0 + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int KELEMS = KIND == 0 ? 64 : 32;
+  constexpr int UMMA_K_BYTES = 32;
+
+  // Global tile t -> (problem, row panel, column panel, k blocks).
+  auto resolve = [&](int t, int& q, int& tm, int& tn, int& nkb) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    q = lo;
+    const int tiles_m = probs[q].ld / BM;
+    tile_coords(t - probs[q].tile0, tiles_m, tiles_m, tm, tn);
+    nkb = probs[q].ld / KELEMS;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 4);
+    }
+    mbar_init(drain, 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long issued = 0, it = 0;
+      int fenced = -1;
+      for (int t = blockIdx.x; t < ntiles && !*s_fail; t += gridDim.x) {
+        int q, tm, tn, nkb;
+        resolve(t, q, tm, tn, nkb);
+        const CUtensorMap* ma = &probs[q].ma;
+        const CUtensorMap* mb = &probs[q].mb;
+        if (q != fenced) {
+          // The descriptor array is rewritten between launches at the same
+          // address: make the tensor-map proxy see the current maps.
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ma)
+                       : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mb)
+                       : "memory");
+          fenced = q;
+        }
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int st = (int)(it % STAGES);
+          const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+          if (it >= STAGES && !mbar_wait(empty0 + 8 * st, ph ^ 1, limit_ns)) {
+            *s_fail = 1;
+            break;
+          }
+          if (*s_fail) break;
+          const uint32_t fb = full0 + 8 * st;
+          mbar_expect_tx(fb, C::STAGE_BYTES);
+          tma_load_2d(sbase + st * C::STAGE_BYTES, ma, kb * KELEMS, tm * BM, fb);
+          tma_load_2d(sbase + st * C::STAGE_BYTES + A_BYTES, mb, kb * KELEMS, tn * BN, fb);
+          issued = it + 1;
+        }
+      }
+      if (*s_fail) {
+        for (long long k = issued > STAGES ? issued - STAGES : 0; k < issued; ++k)
+          mbar_wait(full0 + 8 * (int)(k % STAGES), (uint32_t)((k / STAGES) & 1), limit_ns);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(KIND, BN);
+      long long it = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        int q, tm, tn, nkb;
+        resolve(t, q, tm, tn, nkb);
+        const int buf = i & 1;
+        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+        if (i >= 2 && !mbar_wait(acce0 + 8 * buf, ((i >> 1) & 1) ^ 1, limit_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int st = (int)(it % STAGES);
+          if (!mbar_wait(full0 + 8 * st, (uint32_t)((it / STAGES) & 1), limit_ns) || *s_fail) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_addr = sbase + st * C::STAGE_BYTES;
+          const uint32_t b_addr = a_addr + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < ROW_BYTES / UMMA_K_BYTES; ++k) {
+            mma<KIND>(acc, smem_desc_sw128(a_addr + k * UMMA_K_BYTES),
+                      smem_desc_sw128(b_addr + k * UMMA_K_BYTES), idesc, (kb | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(empty0 + 8 * st);
+        }
+        if (!ok) break;
+        mma_commit(accf0 + 8 * buf);
+      }
+      if (!ok) {
+        *s_fail = 1;
+        mma_commit(drain);
+        mbar_wait(drain, 0, limit_ns);
+      }
+    }
+  } else {
+    const int qw = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      if (!mbar_wait(accf0 + 8 * buf, (uint32_t)((i >> 1) & 1), limit_ns) || *s_fail) {
+        *s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      int q, tm, tn, nkb;
+      resolve(t, q, tm, tn, nkb);
+      const int ld = probs[q].ld, n = probs[q].n;
+      void* Cq = probs[q].C;
+      unsigned long long* cmax = probs[q].cmax;
+      float lmax = -INFINITY;
+      const int row = tm * BM + qw * 32 + lane;
+      const uint32_t acc = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(acc + c0, v);
+        const int col0 = tn * BN + c0;
+        if (cmax != nullptr && row < n) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            if (col0 + e < n) lmax = fmaxf(lmax, v[e]);
+        }
+        if (out_kind == 1) {
+          __nv_bfloat162 h[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+          uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cq) +
+                                                (size_t)row * ld + col0);
+          dst[0] = *reinterpret_cast<uint4*>(&h[0]);
+          dst[1] = *reinterpret_cast<uint4*>(&h[4]);
+        } else {
+          if (out_kind == 2) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = to_tf32(v[e]);
+          }
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(Cq) + (size_t)row * ld + col0);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * buf)
+                                  : "memory");
+      if (cmax != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        if (lane == 0 && lmax > -INFINITY) atomicMax(cmax, ordered_key((double)lmax));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(C::TMEM_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && *s_fail) {
+    // A wait expired: every problem of the launch is reported failed.
+    for (int q = 0; q < nprob; ++q) atomicExch(probs[q].err, DEV_TIMEOUT);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (fn == nullptr) {
@@ -447,6 +664,57 @@ int launch_k(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, in
 }
 
 }  // namespace
+
+bool make_group_problem(GemmGroupProblem* q, const void* A, const void* Bop, void* C, int ld,
+                        int n, int kind, unsigned long long* cmax, int* err) {
+  if (ld % 128 != 0 || ld <= 0) return false;
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bop) |
+       reinterpret_cast<uintptr_t>(C)) & 15)
+    return false;
+  if (!make_map(&q->ma, A, ld, kind, BM) || !make_map(&q->mb, Bop, ld, kind, 128)) return false;
+  q->C = C;
+  q->cmax = cmax;
+  q->err = err;
+  q->ld = ld;
+  q->n = n;
+  q->tile0 = 0;
+  return true;
+}
+
+int launch_gemm_tc_group(GemmGroupProblem* hp, int count, int kind, int out_kind, void* dp,
+                         size_t dp_bytes, uint64_t limit_ns, cudaStream_t s) {
+  if (count < 1) return 0;
+  if ((size_t)count * sizeof(GemmGroupProblem) > dp_bytes ||
+      (reinterpret_cast<uintptr_t>(dp) & 63))
+    return -1;
+  int total = 0;
+  for (int q = 0; q < count; ++q) {
+    hp[q].tile0 = total;
+    total += (hp[q].ld / BM) * (hp[q].ld / BM);
+  }
+  if (cudaMemcpyAsync(dp, hp, (size_t)count * sizeof(GemmGroupProblem), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return -1;
+  static DeviceCache attr[2];
+  if (device_cached(attr[kind], [kind] {
+        const void* f = kind == 0 ? (const void*)gemm_tc_group_kernel<0>
+                                  : (const void*)gemm_tc_group_kernel<1>;
+        return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cfg<128>::SMEM_BYTES) == cudaSuccess
+                   ? 1
+                   : -1;
+      }) < 0)
+    return -1;
+  const int grid = total < num_sms_cached() ? total : num_sms_cached();
+  const GemmGroupProblem* d = static_cast<const GemmGroupProblem*>(dp);
+  if (kind == 0)
+    gemm_tc_group_kernel<0><<<grid, GEMM_THREADS, Cfg<128>::SMEM_BYTES, s>>>(d, count, total,
+                                                                            out_kind, limit_ns);
+  else
+    gemm_tc_group_kernel<1><<<grid, GEMM_THREADS, Cfg<128>::SMEM_BYTES, s>>>(d, count, total,
+                                                                            out_kind, limit_ns);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int kind, int out_kind,
                    const double* Kmat, double lam, unsigned long long* cmax, int* err,

@@ -251,6 +251,7 @@ struct SdsnLaunch {
   int in_fp32 = 0;             // X is FP32
   int out_fp32 = 0;            // Y and the sweep arithmetic are FP32
   int mode = 0;                // 0: scale X (Alg. 2 step 1); 1: continue from Y0 = X
+  int barrier_zeroed = 0;      // the caller zeroed *barrier already (grouped launches)
   double theta, gamma_tol;
   int max_sweeps;
   const unsigned long long* xmax_key;   // max(X) as an ordered key (mode 0)

@@ -74,12 +74,11 @@ __global__ void transpose_lp_kernel(const double* __restrict__ src, void* __rest
 // low-precision copy of the new N for the next gradient.  Deterministic
 // delta: fixed tile ownership, fixed reduction trees, last-block combine.
 template <int KIND>
-__global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ N,
-                                                           const double* __restrict__ D, int ld,
-                                                           int n, double alpha,
-                                                           void* __restrict__ Nt,
-                                                           double* __restrict__ partials,
-                                                           unsigned* ticket, IterStats* st) {
+__device__ __forceinline__ void update_mixed_body(double* __restrict__ N,
+                                                  const double* __restrict__ D, int ld, int n,
+                                                  double alpha, void* __restrict__ Nt,
+                                                  double* __restrict__ partials, unsigned* ticket,
+                                                  IterStats* st, const int blk, const int nblk) {
   __shared__ double tile[kT][kT + 1];
   __shared__ double red[2][8];
   __shared__ int s_last;
@@ -87,7 +86,7 @@ __global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ 
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int tiles = (n + kT - 1) / kT;
   double d2 = 0.0, n2 = 0.0;
-  for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x) {
+  for (int t = blk; t < tiles * tiles; t += nblk) {
     const int i0 = (t / tiles) * kT, j0 = (t % tiles) * kT;
     for (int r = ty; r < kT; r += 8) {
       const int i = i0 + r, j = j0 + tx;
@@ -123,10 +122,10 @@ __global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ 
     a = warp_sum(a);
     b = warp_sum(b);
     if (lane == 0) {
-      partials[2 * blockIdx.x] = a;
-      partials[2 * blockIdx.x + 1] = b;
+      partials[2 * blk] = a;
+      partials[2 * blk + 1] = b;
       __threadfence();
-      s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+      s_last = (atomicAdd(ticket, 1u) == nblk - 1);
     }
   }
   __syncthreads();
@@ -134,7 +133,7 @@ __global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ 
   __threadfence();
   if (warp == 0) {
     double a = 0.0, b = 0.0;
-    for (int k = lane; k < (int)gridDim.x; k += 32) {
+    for (int k = lane; k < nblk; k += 32) {
       a += __ldcg(&partials[2 * k]);
       b += __ldcg(&partials[2 * k + 1]);
     }
@@ -147,6 +146,39 @@ __global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ 
       *ticket = 0u;
     }
   }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) update_mixed_kernel(double* __restrict__ N,
+                                                           const double* __restrict__ D, int ld,
+                                                           int n, double alpha,
+                                                           void* __restrict__ Nt,
+                                                           double* __restrict__ partials,
+                                                           unsigned* ticket, IterStats* st) {
+  update_mixed_body<KIND>(N, D, ld, n, alpha, Nt, partials, ticket, st, (int)blockIdx.x,
+                          (int)gridDim.x);
+}
+
+// The updates of many problems in one launch: problem q owns CTAs
+// [blk0_q, blk0_q + nblk_q), the same number its solo launch uses, and each
+// of those CTAs runs exactly what the solo CTA of that index runs (same
+// tiles, same reduction tree), so N and delta are bit-identical to solo.
+template <int KIND>
+__global__ void __launch_bounds__(256) update_mixed_group_kernel(const UpdGroupProblem* probs,
+                                                                 int nprob) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].blk0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const UpdGroupProblem& q = probs[lo];
+  update_mixed_body<KIND>(q.N, q.D, q.ld, q.n, q.alpha, q.Nt, q.partials, q.ticket, q.st,
+                          (int)blockIdx.x - q.blk0, q.nblk);
+}
+
+int update_grid(int n) {
+  const int tiles = ((n + kT - 1) / kT) * ((n + kT - 1) / kT);
+  return tiles < 1184 ? tiles : 1184;
 }
 
 int blocks_for(size_t count) {
@@ -193,11 +225,31 @@ int launch_transpose_lp(const double* src, void* dst, int ld, int kind, cudaStre
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+int launch_update_mixed_group(UpdGroupProblem* hp, int count, int kind, void* dp,
+                              size_t dp_bytes, cudaStream_t s) {
+  if (count < 1) return 0;
+  if ((size_t)count * sizeof(UpdGroupProblem) > dp_bytes) return -1;
+  int total = 0;
+  for (int q = 0; q < count; ++q) {
+    hp[q].blk0 = total;
+    hp[q].nblk = update_grid(hp[q].n);
+    total += hp[q].nblk;
+  }
+  if (cudaMemcpyAsync(dp, hp, (size_t)count * sizeof(UpdGroupProblem), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return -1;
+  const UpdGroupProblem* d = static_cast<const UpdGroupProblem*>(dp);
+  if (kind == 0)
+    update_mixed_group_kernel<0><<<total, dim3(32, 8), 0, s>>>(d, count);
+  else
+    update_mixed_group_kernel<1><<<total, dim3(32, 8), 0, s>>>(d, count);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_update_mixed(double* N, const double* D, int ld, int n, double alpha, void* Nt,
                         int kind, double* partials, unsigned* ticket, IterStats* st,
                         cudaStream_t s) {
-  const int tiles = ((n + kT - 1) / kT) * ((n + kT - 1) / kT);
-  const int grid = tiles < 1184 ? tiles : 1184;
+  const int grid = update_grid(n);
   if (kind == 0)
     update_mixed_kernel<0><<<grid, dim3(32, 8), 0, s>>>(N, D, ld, n, alpha, Nt, partials, ticket,
                                                         st);

@@ -82,6 +82,40 @@ __device__ __forceinline__ float relu(float y) {
   return __int_as_float(b & ~(b >> 31));
 }
 
+// Sum of v[0..7] over the 32 lanes of a warp, transposed: afterwards lane l
+// holds the total of entry ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 +
+// ((l >> 2) & 1) (lanes l..l^3 agree).  9 additions per warp for 8 row sums
+// instead of 40 -- FP64 additions are scarce on this GPU.  Fixed order.
+template <typename T>
+__device__ __forceinline__ T transpose_reduce8(T (&v)[8], int lane) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const bool hi = lane & 16;
+    const T send = hi ? v[m] : v[m + 4];
+    const T keep = hi ? v[m + 4] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const bool hi = lane & 8;
+    const T send = hi ? v[m] : v[m + 2];
+    const T keep = hi ? v[m + 2] : v[m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool hi = lane & 4;
+    const T send = hi ? v[0] : v[1];
+    const T keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  T r = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+  return r + __shfl_xor_sync(0xffffffffu, r, 1);
+}
+
+__device__ __forceinline__ int transpose_index8(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
 // VEC consecutive elements of U at p: one 16/8/4-byte access when `vec`
 // (the address is then VEC*sizeof(U)-aligned), element by element otherwise
 // or when the vector would cross `lim` (elements valid: p[0 .. lim-1]).
@@ -186,6 +220,54 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
         }
       }
     };
+    // One row: the pass of eq. 7 (or step 1) on its groups; returns this
+    // lane's part of the row sum.
+    auto do_row = [&](int i, T (&src)[MAXC][VEC]) {
+      T* row = tile + (size_t)i * ldt;
+      const T ai = FIRST ? T(0) : arow[i] + cS;
+      T racc = T(0);
+#pragma unroll
+      for (int s = 0; s < MAXC; ++s) {
+        const int j0 = (lane + 32 * s) * VEC;
+        if (j0 < nc) {
+          T bv[VEC];
+          if (!FIRST) vec_load<T, VEC>(bcol + j0, true, nc - j0, bv);
+          T y[VEC];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            if (FIRST)
+              y[v] = p.mode == 0 ? src[s][v] * scale : src[s][v];
+            else
+              y[v] = relu((src[s][v] + ai) - bv[v]);
+            if (j0 + v >= nc) y[v] = T(0);
+            racc += y[v];
+            cacc[s][v] += y[v];
+          }
+          vec_store<T, VEC>(row + j0, vdst, nc - j0, y);
+        }
+      }
+      return racc;
+    };
+    if constexpr (sizeof(T) == 8 && MAXC <= 6) {
+      // FP64: row sums of 8 rows at a time with one transposed reduction
+      // (the 12-group variant keeps the per-row reduction: its registers are
+      // already taken by the groups).
+      for (int ib = warp; ib < nr; ib += 8 * kSdsnWarps) {
+        T rb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int iu = ib + u * kSdsnWarps;
+          rb[u] = T(0);
+          if (iu < nr) {
+            load_row(iu, cur);
+            rb[u] = do_row(iu, cur);
+          }
+        }
+        const T rs = transpose_reduce8(rb, lane);
+        const int ir = ib + transpose_index8(lane) * kSdsnWarps;
+        if ((lane & 3) == 0 && ir < nr) rowsum[ir] = rs;
+      }
+    } else {
     int i = warp;
     if (i < nr) load_row(i, cur);
     for (; i < nr; i += kSdsnWarps) {
@@ -224,6 +306,7 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
       } else if (inext < nr) {
         load_row(inext, cur);
       }
+    }
     }
 #pragma unroll
     for (int s = 0; s < MAXC; ++s) {
@@ -643,7 +726,9 @@ int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* dd
     k.bar = L[i].barrier;
     k.limit_ns = L[i].limit_ns;
     set_vec_flags(k);
-    if (cudaMemsetAsync(L[i].barrier, 0, sizeof(GridBarrier), s) != cudaSuccess) return -1;
+    if (!L[i].barrier_zeroed &&
+        cudaMemsetAsync(L[i].barrier, 0, sizeof(GridBarrier), s) != cudaSuccess)
+      return -1;
   }
   if (count * sizeof(SdsnK<T, TIn>) > ddesc_bytes) return -1;
   if (cudaMemcpyAsync(ddesc, ks.data(), count * sizeof(SdsnK<T, TIn>), cudaMemcpyHostToDevice,

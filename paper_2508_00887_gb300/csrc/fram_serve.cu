@@ -5,10 +5,15 @@
 //   * admission: waiting requests get a device slot (A, B, N, X and the
 //     low-precision shadows stay resident until the request retires) while
 //     the HBM budget has room; freed slots are cached and reused;
-//   * one tick = one outer iteration of every active request: per-request
-//     gradient GEMMs, then ONE grouped SDSN launch for all requests of a
-//     precision class (each on its own sub-grid with its own barrier and stop
-//     test), the grouped FP64 polish, and the per-request updates;
+//   * one tick = one outer iteration of every active request, in a number
+//     of launches that does not grow with the number of requests (mixed
+//     precision): one kernel clears every slot's per-iteration state, one
+//     grouped tensor-core launch per GEMM of step 5 and input precision
+//     (each request's tiles computed exactly as its solo launch computes
+//     them), the grouped FP32 SDSN (one cluster per request for n <= 1024,
+//     co-resident sub-grids otherwise), the grouped FP64 polish, and one
+//     grouped update per precision; FP64 requests keep per-request GEMMs
+//     and updates;
 //   * stats of all active requests come back in one copy per tick; requests
 //     that stopped (delta, rounding floor, cap, or an error) retire: LAP and
 //     objective on the device, results copied to host, slot released;
@@ -65,6 +70,7 @@ struct Request {
          *T64 = nullptr;
   void *Alp = nullptr, *Blp = nullptr, *Nt = nullptr, *Tlp = nullptr;
   float* X32 = nullptr;
+  GemmGroupProblem g1{}, g2{};  // T = A N and X = T B as grouped-GEMM problems
   double *spart = nullptr, *upart = nullptr;
   void* lap_ws = nullptr;
   int32_t* perm = nullptr;
@@ -94,6 +100,9 @@ struct Serve {
   SlotStats* dstats = nullptr;
   SlotStats* hstats = nullptr;
   void* ddesc = nullptr;
+  void* gdesc[2] = {nullptr, nullptr};  // grouped GEMM problems (64-byte aligned)
+  void* udesc = nullptr;                // grouped update problems
+  uint64_t ticks = 0;
   std::vector<int> free_ids;
   std::vector<std::pair<size_t, char*>> cache;  // free slot blocks
   size_t budget = 0;
@@ -199,6 +208,20 @@ bool sv_ok(fram_ctx* c, int launched) {
 }
 #define SV_OK(x) sv_ok(c, (x))
 
+// Clear the per-iteration state of every slot (IterStats, the max key and
+// both SDSN barriers) in one launch, instead of three memsets per request.
+__global__ void tick_prologue_kernel(SlotStats* st, int count) {
+  SlotStats& s = st[blockIdx.x];
+  if (blockIdx.x >= (unsigned)count) return;
+  int* it = reinterpret_cast<int*>(&s.it);
+  for (unsigned k = threadIdx.x; k < sizeof(IterStats) / sizeof(int); k += blockDim.x) it[k] = 0;
+  if (threadIdx.x == 0) {
+    s.xmax = 0ull;
+    s.bar32 = GridBarrier{};
+    s.bar64 = GridBarrier{};
+  }
+}
+
 void serve_loop(fram_ctx* c, Serve* Sp) {
   Serve& S = *Sp;
   cudaSetDevice(c->device);
@@ -273,6 +296,14 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
           SV_OK(launch_convert_lp(r->As, r->Alp, r->ld, r->kind, s));
           SV_OK(launch_convert_lp(r->Bs, r->Blp, r->ld, r->kind, s));
           SV_OK(launch_transpose_lp(r->N, r->Nt, r->ld, r->kind, s));
+          SlotStats* sst = &S.dstats[r->sid];
+          if (!make_group_problem(&r->g1, r->Alp, r->Nt, r->Tlp, r->ld, r->n, r->kind, nullptr,
+                                  &sst->it.gemm_err) ||
+              !make_group_problem(&r->g2, r->Tlp, r->Blp, r->X32, r->ld, r->n, r->kind,
+                                  &sst->xmax, &sst->it.gemm_err)) {
+            finish(S, r, FRAM_ERR_CUDA, "tensor map encode failed");
+            continue;
+          }
         }
         r->prepped = true;
         std::lock_guard<std::mutex> lk(S.mu);
@@ -286,12 +317,14 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
     }
     if (act.empty()) continue;
     // One outer iteration of every active request.
-    std::vector<SdsnLaunch> L64, L32, Lpol;
+    ++S.ticks;
     bool ok = true;
+    tick_prologue_kernel<<<kMaxActive, 64, 0, s>>>(S.dstats, kMaxActive);
+    ok = SV_OK(cudaPeekAtLastError() == cudaSuccess ? 1 : -1) && ok;
+    std::vector<SdsnLaunch> L64, L32, Lpol;
+    std::vector<GemmGroupProblem> gp1[2], gp2[2];
     for (Request* r : act) {
       SlotStats* st = &S.dstats[r->sid];
-      cudaMemsetAsync(&st->xmax, 0, sizeof(unsigned long long), s);
-      cudaMemsetAsync(&st->it, 0, sizeof(IterStats), s);
       SdsnLaunch L{};
       L.n = r->n;
       L.ldx = L.ldy = r->ld;
@@ -300,6 +333,7 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       L.stats = &st->it.sdsn;
       L.partials = r->spart;
       L.limit_ns = c->wait_limit_ns;
+      L.barrier_zeroed = 1;
       if (!r->mixed) {
         ok = SV_OK(launch_dgemm(r->As, r->N, r->T64, r->ld, r->n, nullptr, 0.0, nullptr, s)) && ok;
         ok = SV_OK(launch_dgemm(r->T64, r->Bs, r->X64, r->ld, r->n, nullptr, 0.0, &st->xmax, s)) && ok;
@@ -309,11 +343,8 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
         L.barrier = &st->bar64;
         L64.push_back(L);
       } else {
-        ok = SV_OK(launch_gemm_tc(r->Alp, r->Nt, r->Tlp, r->ld, r->n, r->kind,
-                                  r->kind == 0 ? 1 : 2, nullptr, 0.0, nullptr, &st->it.gemm_err,
-                                  c->wait_limit_ns, s)) && ok;
-        ok = SV_OK(launch_gemm_tc(r->Tlp, r->Blp, r->X32, r->ld, r->n, r->kind, 0, nullptr, 0.0,
-                                  &st->xmax, &st->it.gemm_err, c->wait_limit_ns, s)) && ok;
+        gp1[r->kind].push_back(r->g1);
+        gp2[r->kind].push_back(r->g2);
         const double tol32 = std::max(r->p.polish_tol, r->p.gamma_tol);
         L.X = L.Y = r->X32;
         L.in_fp32 = L.out_fp32 = 1;
@@ -334,6 +365,16 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
         P.barrier = &st->bar64;
         Lpol.push_back(P);
       }
+    }
+    // Step 5: one grouped launch per GEMM and input precision.
+    const size_t gbytes = kMaxActive * sizeof(GemmGroupProblem);
+    for (int kind = 0; kind < 2 && ok; ++kind) {
+      if (gp1[kind].empty()) continue;
+      ok = SV_OK(launch_gemm_tc_group(gp1[kind].data(), (int)gp1[kind].size(), kind,
+                                      kind == 0 ? 1 : 2, S.gdesc[0], gbytes, c->wait_limit_ns,
+                                      s)) && ok;
+      ok = ok && SV_OK(launch_gemm_tc_group(gp2[kind].data(), (int)gp2[kind].size(), kind, 0,
+                                            S.gdesc[1], gbytes, c->wait_limit_ns, s));
     }
     // Grouped SDSN launches.  Every request keeps the sub-grid that
     // fram_solve would give it alone (so its arithmetic, and its result, do
@@ -369,15 +410,33 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       waves(grid32);
     }
     waves(Lpol);
+    // Steps 7-8: one grouped update per precision (FP64 requests alone).
+    std::vector<UpdGroupProblem> up[2];
     for (Request* r : act) {
       SlotStats* st = &S.dstats[r->sid];
-      if (!r->mixed)
+      if (!r->mixed) {
         ok = SV_OK(launch_update(r->N, r->ld, r->X64, r->ld, r->n, r->p.alpha, &st->it, r->upart,
                                  &st->ticket_upd, s)) && ok;
-      else
-        ok = SV_OK(launch_update_mixed(r->N, r->X64, r->ld, r->n, r->p.alpha, r->Nt, r->kind,
-                                       r->upart, &st->ticket_upd, &st->it, s)) && ok;
+      } else {
+        UpdGroupProblem u{};
+        u.N = r->N;
+        u.D = r->X64;
+        u.Nt = r->Nt;
+        u.partials = r->upart;
+        u.ticket = &st->ticket_upd;
+        u.st = &st->it;
+        u.alpha = r->p.alpha;
+        u.ld = r->ld;
+        u.n = r->n;
+        up[r->kind].push_back(u);
+      }
     }
+    for (int kind = 0; kind < 2 && ok; ++kind)
+      if (!up[kind].empty())
+        ok = SV_OK(launch_update_mixed_group(up[kind].data(), (int)up[kind].size(), kind,
+                                             kind == 0 ? S.udesc : static_cast<char*>(S.udesc) +
+                                                             kMaxActive * sizeof(UpdGroupProblem),
+                                             kMaxActive * sizeof(UpdGroupProblem), s)) && ok;
     cudaMemcpyAsync(S.hstats, S.dstats, kMaxActive * sizeof(SlotStats), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (!ok || e != cudaSuccess) {
@@ -463,7 +522,10 @@ Serve* get_serve(fram_ctx* c, fram_status* st) {
             cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc(&S->dstats, kMaxActive * sizeof(SlotStats)) == cudaSuccess &&
             cudaMallocHost(&S->hstats, kMaxActive * sizeof(SlotStats)) == cudaSuccess &&
-            cudaMalloc(&S->ddesc, sdsn_group_desc_bytes(kMaxActive)) == cudaSuccess;
+            cudaMalloc(&S->ddesc, sdsn_group_desc_bytes(kMaxActive)) == cudaSuccess &&
+            cudaMalloc(&S->gdesc[0], kMaxActive * sizeof(GemmGroupProblem)) == cudaSuccess &&
+            cudaMalloc(&S->gdesc[1], kMaxActive * sizeof(GemmGroupProblem)) == cudaSuccess &&
+            cudaMalloc(&S->udesc, 2 * kMaxActive * sizeof(UpdGroupProblem)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     *st = FRAM_ERR_OOM;
@@ -472,6 +534,8 @@ Serve* get_serve(fram_ctx* c, fram_status* st) {
     if (S->dstats) cudaFree(S->dstats);
     if (S->hstats) cudaFreeHost(S->hstats);
     if (S->ddesc) cudaFree(S->ddesc);
+    for (void* d : {S->gdesc[0], S->gdesc[1], S->udesc})
+      if (d) cudaFree(d);
     delete S;
     return nullptr;
   }
@@ -503,6 +567,9 @@ void serve_shutdown(fram_ctx* c) {
   cudaFree(S->dstats);
   cudaFreeHost(S->hstats);
   cudaFree(S->ddesc);
+  cudaFree(S->gdesc[0]);
+  cudaFree(S->gdesc[1]);
+  cudaFree(S->udesc);
   c->serve_bytes = 0;
   delete S;
   c->serve = nullptr;
@@ -511,6 +578,11 @@ void serve_shutdown(fram_ctx* c) {
 }  // namespace fram
 
 using namespace fram;
+
+extern "C" uint64_t fram_serve_ticks(const fram_ctx* c) {
+  if (!c || !c->serve) return 0;
+  return static_cast<const Serve*>(c->serve)->ticks;
+}
 
 extern "C" fram_status fram_submit(fram_ctx* c, int n, const double* A, const double* B,
                                    const fram_params* params, uint64_t* ticket) {
