@@ -360,6 +360,22 @@ def run_batch(args):
     ms = [a.elapsed_time(b) for a, b in ev]
     total_s = max_over_ranks(sum(ms) / 1e3, ws)
     value = job_rate(args.steps * len(pairs), ws, total_s)
+    chosen = fr.fram_batched_kernel(ctx, PRECISIONS[args.precision])
+    # Each kernel form the autotuner chose among, timed on the whole batch
+    # (one call each, L2 flushed before), for the record.
+    forms = {}
+    names = {1: "cta128", 2: "cta256", 3: "cta512", 4: "team_split32", 5: "team_edge64"}
+    for v in (1, 2, 3, 4, 5) if args.precision != "fp64" else (1, 2, 3):
+        fr.fram_set_batched_kernel(ctx, v)
+        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)   # tune/capture
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        forms[names[v]] = e0.elapsed_time(e1)
+    fr.fram_set_batched_kernel(ctx, 0)
     # End to end with host buffers (pinned): packing, copies and unpacking inside.
     Ah = [torch.from_numpy(g.A).pin_memory().numpy() for g in pairs]
     Bh = [torch.from_numpy(g.B).pin_memory().numpy() for g in pairs]
@@ -379,7 +395,10 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision != "fp64" else "f64", "data": "synthetic",
             "config": {"workload": BATCH_DESC, "pairs": len(pairs), "precision": args.precision,
-                       "l2": "flushed between timed steps (256 MiB write)"},
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "kernel_form": {1: "cta128", 2: "cta256", 3: "cta512", 4: "team_split32",
+                                       5: "team_edge64"}.get(chosen, str(chosen)),
+                       "forms_ms": forms},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
             "solve": {"mean_accuracy": acc,
                       "mean_outer_iters": float(np.mean([i.outer_iters for i in infos])),

@@ -184,6 +184,18 @@ fram_status fram_solve_batched(fram_ctx *ctx, int count, const int *n, const dou
                                const double *const *B, const fram_params *params,
                                double *const *X_out, int32_t *const *perm_out, fram_info *infos);
 
+/* Kernel form of fram_solve_batched's persistent launch (an autotuning and
+ * testing hook).  0 (default): on the first call per precision, time every
+ * form on a prefix of the batch and keep the fastest.  1, 2, 3: one pair per
+ * CTA of 128, 256 or 512 threads (FP64 and mixed).  4: teams of two warps,
+ * a pair with n <= 32 on one warp (tile edge 32), a larger one on both
+ * (tile edge 64); 5: every pair on two warps (mixed precision only; an FP64
+ * batch with 4 or 5 returns FRAM_ERR_INVALID).  FRAM_ERR_INVALID outside 0..5. */
+fram_status fram_set_batched_kernel(fram_ctx *ctx, int variant);
+
+/* The form the batched path uses for `precision` (0 before its first call). */
+int fram_batched_kernel(const fram_ctx *ctx, int precision);
+
 /* ------------------------------------------------------------- serving */
 
 /* Enqueue one problem for the context's continuous-batching scheduler (a

@@ -90,6 +90,8 @@ def load(path: str | None = None):
         "fram_solve": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P, C.POINTER(FramInfo)]),
         "fram_solve_batched": (i, [_P, i, _P, _P, _P, C.POINTER(FramParams), _P, _P,
                                    C.POINTER(FramInfo)]),
+        "fram_set_batched_kernel": (i, [_P, i]),
+        "fram_batched_kernel": (i, [_P, i]),
         "fram_submit": (i, [_P, i, _P, _P, C.POINTER(FramParams), C.POINTER(u64)]),
         "fram_poll": (i, [_P, u64, _P, _P, C.POINTER(FramInfo), i]),
         "fram_serve_ticks": (u64, [_P]),
@@ -117,7 +119,8 @@ def exported_symbols():
     """Names the header declares; used by the ABI test."""
     return ["fram_create", "fram_destroy", "fram_default_params", "fram_last_error",
             "fram_kernel_launches", "fram_set_wait_limit", "fram_selftest_wait_timeout",
-            "fram_solve", "fram_solve_batched", "fram_submit",
+            "fram_solve", "fram_solve_batched", "fram_set_batched_kernel", "fram_batched_kernel",
+            "fram_submit",
             "fram_poll", "fram_serve_ticks", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_f32", "fram_sdsn_grouped",
             "fram_assign", "fram_sdsn_static"]
 
@@ -220,6 +223,17 @@ def fram_solve_batched(ctx, ns, As, Bs, params=None, X_outs=None, perm_outs=None
     if check:
         _check(ctx, st)
     return st, list(infos)[:count]
+
+
+def fram_set_batched_kernel(ctx, variant, check=True):
+    st = load().fram_set_batched_kernel(ctx, variant)
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def fram_batched_kernel(ctx, precision) -> int:
+    return int(load().fram_batched_kernel(ctx, precision))
 
 
 def fram_submit(ctx, n, A, B, params=None, check=True):

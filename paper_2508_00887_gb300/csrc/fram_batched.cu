@@ -51,6 +51,7 @@ struct BatchArgs {
   unsigned* queue;
   double lam, alpha, theta, delta_tol, gamma_tol, mixed_delta_tol, stall_ratio, stall_below;
   int max_outer, max_sweeps, use_stall;
+  int team_split;  // team kernel: pairs with n > team_split run on two warps (tile edge 64)
 };
 
 enum : int { PAIR_OK = 0, PAIR_INVALID = 1, PAIR_DEGENERATE = 2 };
@@ -567,6 +568,432 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) batched_kernel(BatchArg
   }
 }
 
+// ------------------------------------------------------------ team kernel
+// The FP32 form for the keypoint-sized pairs: a CTA of 4 warps holds two
+// teams of two warps.  A pair with n <= 32 runs on ONE warp (tile edge 32),
+// a pair with 32 < n <= 64 on a team of two (tile edge 64).  Lane c owns
+// column c of the tile: its column of N and of the SDSN iterate stay in
+// registers for the whole solve, so a sweep (eq. 7) keeps the column sums in
+// the lane, forms the row sums by one transposed shuffle tree (two warps add
+// their halves through shared memory) and synchronises with __syncwarp or a
+// 64-thread named barrier -- no CTA-wide barrier.  The products of step 5
+// read A^T and (A N)^T rows as broadcasts; S and gamma are FP32 double-floats
+// (TwoSum), so no FP64 instruction runs per sweep.
+constexpr int kTeamCT = 128;
+
+template <int TE>
+struct TeamLayout {
+  static constexpr int SA = TE + 4;  // rows of A^T, (A N)^T and N: 16-byte aligned
+  static constexpr int SB = TE + 1;  // B: conflict-free column reads
+  static constexpr size_t a = 0;
+  static constexpr size_t b = a + (size_t)TE * SA * 4;
+  static constexpr size_t t = (b + (size_t)TE * SB * 4 + 15) & ~size_t(15);
+  static constexpr size_t part = t + (size_t)TE * SA * 4;  // [2][TE] row partials
+  static constexpr size_t red = part + 2 * (size_t)TE * 4;  // 8 doubles
+  static constexpr size_t u = red + 64;
+  static constexpr size_t rowmax = u + (size_t)TE * 8;
+  static constexpr size_t rowcol = rowmax + (size_t)TE * 8;
+  static constexpr size_t argc = rowcol + (size_t)TE * 4;
+  static constexpr size_t misc = argc + (size_t)TE * 4;  // 16 ints
+  static constexpr size_t bytes = misc + 64;
+};
+constexpr size_t kTeamBytes = TeamLayout<64>::bytes;
+static_assert(2 * TeamLayout<32>::bytes <= kTeamBytes, "two warp regions in a team region");
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Double-float sum over the 32 lanes (xor butterfly; every lane ends with
+// the same hi + lo, because TwoSum recovers the exact error in any order).
+__device__ __forceinline__ void warp_sum_df(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum_f(hi, oh, s, e);
+    hi = s;
+    lo = (lo + ol) + e;
+  }
+  float s, e;
+  two_sum_f(hi, lo, s, e);
+  hi = s;
+  lo = e;
+}
+
+// Transposed sums of y[0..32) over the 32 lanes: each stage halves the
+// entries a lane carries (the lane whose offset bit is set keeps the upper
+// half), so lane l ends with the warp's total of entry l.  31 shuffles for 32
+// row sums; fixed order; y is read, not modified.
+template <int OFF, int TE>
+__device__ __forceinline__ float team_rows32(const float (&y)[TE], int lane) {
+  float v[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const bool hi = lane & 16;
+    const float send = hi ? y[OFF + m] : y[OFF + m + 16];
+    const float keep = hi ? y[OFF + m + 16] : y[OFF + m];
+    v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int w = 8, o = 8; o > 0; w >>= 1, o >>= 1) {
+#pragma unroll
+    for (int m = 0; m < w; ++m) {
+      const bool hi = lane & o;
+      const float send = hi ? v[m] : v[m + w];
+      const float keep = hi ? v[m + w] : v[m];
+      v[m] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+template <int TE>
+__device__ __forceinline__ void team_sync(int bar_id) {
+  if (TE == 32)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+}
+
+// Team-wide max / sum: warp shuffles, then (TE = 64) the two warps through
+// shared memory in a fixed order.
+template <int TE>
+__device__ __forceinline__ double team_max(double v, double* red, int wt, int bar_id) {
+  v = warp_max(v);
+  if (TE == 32) return v;
+  if ((threadIdx.x & 31) == 0) red[wt] = v;
+  team_sync<TE>(bar_id);
+  const double r = fmax(red[0], red[1]);
+  team_sync<TE>(bar_id);
+  return r;
+}
+template <int TE>
+__device__ __forceinline__ double team_sum(double v, double* red, int wt, int bar_id) {
+  v = warp_sum(v);
+  if (TE == 32) return v;
+  if ((threadIdx.x & 31) == 0) red[wt] = v;
+  team_sync<TE>(bar_id);
+  const double r = red[0] + red[1];
+  team_sync<TE>(bar_id);
+  return r;
+}
+
+// FP32 sums per warp, FP64 across the two warps (as the CTA form's bsum_f).
+template <int TE>
+__device__ __forceinline__ double team_sum_f(float v, double* red, int wt, int bar_id) {
+  const double w = (double)warp_sum(v);
+  if (TE == 32) return w;
+  if ((threadIdx.x & 31) == 0) red[wt] = w;
+  team_sync<TE>(bar_id);
+  const double r = red[0] + red[1];
+  team_sync<TE>(bar_id);
+  return r;
+}
+
+template <int TE>
+__device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, int wt, int bar_id) {
+  using Lay = TeamLayout<TE>;
+  constexpr int SA = Lay::SA, SB = Lay::SB;
+  float* AsT = reinterpret_cast<float*>(region + Lay::a);
+  float* Bs = reinterpret_cast<float*>(region + Lay::b);
+  float* TsT = reinterpret_cast<float*>(region + Lay::t);
+  float* part = reinterpret_cast<float*>(region + Lay::part);
+  double* red = reinterpret_cast<double*>(region + Lay::red);
+  double* u = reinterpret_cast<double*>(region + Lay::u);
+  double* rowmax = reinterpret_cast<double*>(region + Lay::rowmax);
+  int* rowcol = reinterpret_cast<int*>(region + Lay::rowcol);
+  int* argc = reinterpret_cast<int*>(region + Lay::argc);
+  int* misc = reinterpret_cast<int*>(region + Lay::misc);
+  const int lane = threadIdx.x & 31;
+  const int c = TE == 32 ? lane : lane + 32 * wt;  // this lane's column
+  const BatchDesc d = a.desc[pi];
+  const int n = d.n;
+  const double* Ag = a.A + d.off_mat;
+  const double* Bg = a.B + d.off_mat;
+  BatchInfo info{};
+
+  // Validation (Sec. 3, reading (vii)) and the prescale's max, on bit
+  // patterns as in the CTA form.
+  unsigned long long mAb = 0, mBb = 0;
+  double asA = 0.0, asB = 0.0;
+  int badi = 0;
+  for (int e = c; e < n * n; e += TE) {
+    const int i = e / n, j = e - i * n;
+    const unsigned long long xb = (unsigned long long)__double_as_longlong(Ag[e]);
+    const unsigned long long yb = (unsigned long long)__double_as_longlong(Bg[e]);
+    const bool okx = xb < 0x7ff0000000000000ull || xb == 0x8000000000000000ull;
+    const bool oky = yb < 0x7ff0000000000000ull || yb == 0x8000000000000000ull;
+    if (!okx || !oky) {
+      badi = 1;
+      continue;
+    }
+    mAb = mAb > (xb & 0x7fffffffffffffffull) ? mAb : (xb & 0x7fffffffffffffffull);
+    mBb = mBb > (yb & 0x7fffffffffffffffull) ? mBb : (yb & 0x7fffffffffffffffull);
+    const unsigned long long xtb = (unsigned long long)__double_as_longlong(Ag[j * n + i]);
+    const unsigned long long ytb = (unsigned long long)__double_as_longlong(Bg[j * n + i]);
+    if (xtb != xb && xtb < 0x7ff0000000000000ull)
+      asA = fmax(asA, fabs(__longlong_as_double((long long)xb) - __longlong_as_double((long long)xtb)));
+    if (ytb != yb && ytb < 0x7ff0000000000000ull)
+      asB = fmax(asB, fabs(__longlong_as_double((long long)yb) - __longlong_as_double((long long)ytb)));
+  }
+  const double bad = team_max<TE>(badi ? 1.0 : 0.0, red, wt, bar_id);
+  const double mA = team_max<TE>(__longlong_as_double((long long)mAb), red, wt, bar_id);
+  const double mB = team_max<TE>(__longlong_as_double((long long)mBb), red, wt, bar_id);
+  asA = team_max<TE>(asA, red, wt, bar_id);
+  asB = team_max<TE>(asB, red, wt, bar_id);
+  const double cc = fmax(mA, mB);
+  if (bad > 0.0 || asA > 1e-12 * fmax(mA, 1.0) || asB > 1e-12 * fmax(mB, 1.0))
+    info.status = PAIR_INVALID;
+  else if (!(cc > 0.0))
+    info.status = PAIR_DEGENERATE;
+  if (info.status != PAIR_OK) {
+    if (c == 0) a.info[pi] = info;
+    return;
+  }
+  // Alg. 1 steps 2-3 and N0 = 11^T/n (reading (i)); zero padding.
+  const double inv_n = 1.0 / n;
+  const float inv_n_f = (float)inv_n, inv_n2_f = (float)(inv_n * inv_n);
+  const float inv_sq = (float)(1.0 / sqrt(cc));
+  for (int i = 0; i < TE; ++i) {
+    const bool in = i < n && c < n;
+    AsT[c * SA + i] = in ? (float)Ag[i * n + c] * inv_sq : 0.f;  // A^T[c][i] = A[i][c]
+    Bs[i * SB + c] = in ? (float)Bg[i * n + c] * inv_sq : 0.f;
+  }
+  float ncol[TE], y[TE];
+#pragma unroll
+  for (int i = 0; i < TE; ++i) ncol[i] = (i < n && c < n) ? inv_n_f : 0.f;
+  team_sync<TE>(bar_id);
+  const double thr = (double)n * (1.0 + a.gamma_tol);
+  const float thr_hi = (float)thr, thr_lo = (float)(thr - (double)thr_hi);
+  const float al = (float)a.alpha, bl = (float)(1.0 - a.alpha);
+  double prev_delta = INFINITY, delta = INFINITY, g = INFINITY;
+  float Shi = 0.f, Slo = 0.f;
+  int t = 0, sweeps_total = 0;
+  while (t < a.max_outer) {
+    // Step 5, T = A N: column c of T from column c of N and rows of A^T.
+#pragma unroll
+    for (int i = 0; i < TE; ++i) y[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < TE; ++k) {
+      // One k at a time: without the barrier the unrolled loop hoists the
+      // loads of many rows at once and runs out of registers.
+      asm volatile("" ::: "memory");
+      if (k < n) {
+        const float nk = ncol[k];
+        const float4* ar = reinterpret_cast<const float4*>(AsT + k * SA);
+#pragma unroll
+        for (int q = 0; q < TE / 4; ++q) {
+          const float4 av = ar[q];
+          y[4 * q] = fmaf(av.x, nk, y[4 * q]);
+          y[4 * q + 1] = fmaf(av.y, nk, y[4 * q + 1]);
+          y[4 * q + 2] = fmaf(av.z, nk, y[4 * q + 2]);
+          y[4 * q + 3] = fmaf(av.w, nk, y[4 * q + 3]);
+        }
+      }
+    }
+    team_sync<TE>(bar_id);  // the previous iteration's reads of (A N)^T are done
+    {
+      float4* tr = reinterpret_cast<float4*>(TsT + c * SA);  // (A N)^T[c][i] = T[i][c]
+#pragma unroll
+      for (int q = 0; q < TE / 4; ++q)
+        tr[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    }
+    team_sync<TE>(bar_id);
+    // X = T B: column c of X from column c of B and rows of T^T.
+#pragma unroll
+    for (int i = 0; i < TE; ++i) y[i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < TE; ++k) {
+      asm volatile("" ::: "memory");
+      if (k < n) {
+        const float bk = Bs[k * SB + c];
+        const float4* tr = reinterpret_cast<const float4*>(TsT + k * SA);
+#pragma unroll
+        for (int q = 0; q < TE / 4; ++q) {
+          const float4 tv = tr[q];
+          y[4 * q] = fmaf(tv.x, bk, y[4 * q]);
+          y[4 * q + 1] = fmaf(tv.y, bk, y[4 * q + 1]);
+          y[4 * q + 2] = fmaf(tv.z, bk, y[4 * q + 2]);
+          y[4 * q + 3] = fmaf(tv.w, bk, y[4 * q + 3]);
+        }
+      }
+    }
+    float lm = -INFINITY;
+    if (c < n)
+#pragma unroll
+      for (int i = 0; i < TE; ++i)
+        if (i < n) lm = fmaxf(lm, y[i]);
+    const double m = team_max<TE>((double)lm, red, wt, bar_id);
+    if (!(m > 0.0)) {
+      info.status = PAIR_DEGENERATE;
+      break;
+    }
+    // Step 6: SDSN (Alg. 2).  k = 0 is step 1, then the sweeps of eq. 7.
+    const float scale = (float)((a.theta / 2.0) / m);
+    int k = 0;
+    float cS1 = 0.f, bc = 0.f;
+    while (true) {
+      if (k == 0) {
+#pragma unroll
+        for (int i = 0; i < TE; ++i) y[i] *= scale;
+      } else {
+        // a_i = 1/n + S/n^2 - r_i/n for all rows, from the row sums.
+#pragma unroll
+        for (int q = 0; q < TE / 4; ++q) {
+          const float4 r0 = reinterpret_cast<const float4*>(part)[q];
+          float4 r;
+          if (TE == 64) {
+            const float4 r1 = reinterpret_cast<const float4*>(part + TE)[q];
+            r = make_float4(r0.x + r1.x, r0.y + r1.y, r0.z + r1.z, r0.w + r1.w);
+          } else {
+            r = r0;
+          }
+          const float rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int i = 4 * q + h;
+            const float ai = i < n ? cS1 - rr[h] * inv_n_f : -INFINITY;  // padding rows stay 0
+            y[i] = fmaxf((y[i] + ai) - bc, 0.f);
+          }
+        }
+      }
+      ++k;
+      // Sums of the new Y: column (in the lane), rows (transposed tree).
+      float cs = 0.f;
+#pragma unroll
+      for (int i = 0; i < TE; ++i) cs += y[i];
+      // After the trees lane l holds the warp's sum of row l (and, TE = 64,
+      // of row 32 + l): every row by exactly one lane.
+      const float v0 = team_rows32<0>(y, lane);
+      const float v1 = TE == 64 ? team_rows32<TE == 64 ? 32 : 0>(y, lane) : 0.f;
+      team_sync<TE>(bar_id);  // every lane has read the previous row sums
+      part[wt * TE + lane] = v0;
+      if (TE == 64) part[wt * TE + 32 + lane] = v1;
+      team_sync<TE>(bar_id);
+      // S over all rows as a double-float, the same in every lane of the team.
+      float shi, slo = 0.f;
+      if (TE == 32) {
+        shi = v0;
+      } else {
+        two_sum_f(part[lane] + part[TE + lane], part[32 + lane] + part[TE + 32 + lane], shi, slo);
+      }
+      warp_sum_df(shi, slo);
+      Shi = shi;
+      Slo = slo;
+      bc = c < n ? cs * inv_n_f : INFINITY;  // padding column: stays 0
+      cS1 = inv_n_f + (shi * inv_n2_f + slo * inv_n2_f);
+      const bool below = shi < thr_hi || (shi == thr_hi && slo <= thr_lo);
+      if (k > 1 && below) break;  // gamma of the last clamped result (reading (iii))
+      if (k > a.max_sweeps) break;
+    }
+    const int sweeps = k - 1;
+    if (sweeps > 0) g = ((double)Shi + (double)Slo) * inv_n - 1.0;
+    sweeps_total += sweeps;
+    // Steps 7-8 (FP32 N as in the CTA form; delta's block sums in FP64).
+    float d2f = 0.f, nn2f = 0.f;
+    if (c < n) {
+#pragma unroll
+      for (int i = 0; i < TE; ++i) {
+        if (i < n) {
+          const float old = ncol[i];
+          const float nn = fmaf(bl, old, al * y[i]);
+          const float dd = nn - old;
+          ncol[i] = nn;
+          d2f = fmaf(dd, dd, d2f);
+          nn2f = fmaf(nn, nn, nn2f);
+        }
+      }
+    }
+    const double d2 = team_sum_f<TE>(d2f, red, wt, bar_id);
+    const double nn2 = team_sum_f<TE>(nn2f, red, wt, bar_id);
+    ++t;
+    const double dl = sqrt(d2) / sqrt(nn2);
+    bool stop = dl <= a.delta_tol || (a.use_stall && dl <= a.mixed_delta_tol);
+    if (a.use_stall && a.stall_ratio > 0.0 && dl <= a.stall_below && dl > a.stall_ratio * prev_delta)
+      stop = true;
+    prev_delta = dl;
+    delta = dl;
+    if (stop) break;
+  }
+  if (info.status != PAIR_OK) {
+    if (c == 0) a.info[pi] = info;
+    team_sync<TE>(bar_id);
+    return;
+  }
+  // Step 10 (eq. 2): N into shared memory (over A^T, no longer needed), then
+  // the Hungarian of the CTA form on one warp.
+  team_sync<TE>(bar_id);
+#pragma unroll
+  for (int i = 0; i < TE; ++i) AsT[i * SA + c] = ncol[i];
+  team_sync<TE>(bar_id);
+  if (wt == 0 || TE == 32) small_lap(AsT, SA, n, u, rowcol, argc, rowmax, &misc[0]);
+  team_sync<TE>(bar_id);
+  // Objective (eq. 1) and matching error (Sec. 7) on the unscaled inputs.
+  double s1 = 0.0, s2 = 0.0;
+  for (int e = c; e < n * n; e += TE) {
+    const int i = e / n, j = e - i * n;
+    const double x = Ag[e];
+    const double yv = Bg[rowcol[i] * n + rowcol[j]];
+    s1 = fma(x, yv, s1);
+    s2 = fma(x - yv, x - yv, s2);
+  }
+  const double av = c < n ? (double)AsT[c * SA + rowcol[c]] : 0.0;
+  s1 = team_sum<TE>(s1, red, wt, bar_id);
+  s2 = team_sum<TE>(s2, red, wt, bar_id);
+  const double avs = team_sum<TE>(av, red, wt, bar_id);
+  if (c < n) a.perm[d.off_vec + c] = rowcol[c];
+  if (a.Nout != nullptr && c < n) {
+    double* no = a.Nout + d.off_mat;
+#pragma unroll
+    for (int i = 0; i < TE; ++i)
+      if (i < n) no[i * n + c] = (double)ncol[i];
+  }
+  if (c == 0) {
+    info.outer_iters = t;
+    info.total_sweeps = sweeps_total;
+    info.delta = delta;
+    info.gamma = g;
+    info.objective = 0.5 * s1;
+    info.match_error = 0.5 * sqrt(s2);
+    info.assignment_value = avs;
+    info.lap_aug = misc[0];
+    a.info[pi] = info;
+  }
+  team_sync<TE>(bar_id);
+}
+
+__global__ void __launch_bounds__(kTeamCT, 2) batched_team_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_pi[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int team = warp >> 1, wt = warp & 1;
+  unsigned char* region = smem + team * kTeamBytes;
+  const int bar_id = 1 + team;  // named barrier of the team's 64 threads
+  while (true) {
+    if (wt == 0 && lane == 0) s_pi[team] = (int)atomicAdd(a.queue, 1u);
+    team_sync<64>(bar_id);
+    const int pi = s_pi[team];
+    team_sync<64>(bar_id);
+    if (pi >= a.count) break;
+    if (a.desc[pi].n > a.team_split) {
+      team_solve<64>(a, pi, region, wt, bar_id);
+    } else {
+      // Pairs are queued longest first: every later pair also has n <=
+      // team_split <= 32, so the second warp takes its own.
+      int pj = pi;
+      if (wt == 1) {
+        if (lane == 0) pj = (int)atomicAdd(a.queue, 1u);
+        pj = __shfl_sync(0xffffffffu, pj, 0);
+      }
+      if (pj < a.count) team_solve<32>(a, pj, region + wt * TeamLayout<32>::bytes, 0, bar_id);
+    }
+  }
+}
+
 // Gather caller matrices (device pointers, table by processing position)
 // into the packed input buffers.
 __global__ void gather_kernel(const double* const* srcA, const double* const* srcB,
@@ -599,6 +1026,8 @@ struct BatchedState {
   double *A = nullptr, *B = nullptr, *N = nullptr;
   int32_t* perm = nullptr;
   BatchDesc* desc = nullptr;
+  BatchDesc* tdesc = nullptr;   // autotuner: strided sample of the queue
+  size_t cap_tdesc = 0;
   BatchInfo* info = nullptr;
   void** ptrs = nullptr;        // device tables by position: A, B, X, perm (4 x count)
   unsigned* queue = nullptr;
@@ -608,7 +1037,8 @@ struct BatchedState {
   BatchDesc* hdesc = nullptr;
   BatchInfo* hinfo = nullptr;
   void** hptrs = nullptr;
-  int tuned_nt[2] = {0, 0};     // autotuned block size per precision (0 = not tuned)
+  int tuned_nt[2] = {0, 0};     // autotuned kernel variant per precision (0 = not tuned)
+  int forced = 0;               // fram_set_batched_kernel: 0 = autotune
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   // signature of the captured graph
@@ -669,9 +1099,51 @@ int launch_batched(const BatchArgs& a, int nt, int num_sms, cudaStream_t s) {
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_batched_any(bool fp32, const BatchArgs& a, int nt, int num_sms, cudaStream_t s) {
-  return fp32 ? launch_batched<float>(a, nt, num_sms, s)
-              : launch_batched<double>(a, nt, num_sms, s);
+// Team kernel (FP32): two teams of two warps per CTA, persistent.
+int launch_batched_team(const BatchArgs& a, int num_sms, cudaStream_t s) {
+  static DeviceCache occ;
+  const int per_sm = device_cached(occ, [] {
+    if (cudaFuncSetAttribute(batched_team_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kTeamBytes)) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_team_kernel, kTeamCT,
+                                                      2 * kTeamBytes) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    return v > 0 ? v : -1;
+  });
+  if (per_sm < 1) return -1;
+  // Persistent: every CTA resident at once, none beyond two pairs per CTA.
+  int grid = per_sm * num_sms;
+  if (grid > (a.count + 1) / 2) grid = (a.count + 1) / 2;
+  if (grid < 1) grid = 1;
+  batched_team_kernel<<<grid, kTeamCT, 2 * kTeamBytes, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Kernel variants of the batched path.  CTA form: one pair per CTA of 128,
+// 256 or 512 threads (FP64 and FP32).  Team form (FP32 only): tile edge 32
+// on one warp for n <= 32 and 64 on two warps above, or 64 for every pair.
+enum BatchVariant : int { BV_CTA128 = 1, BV_CTA256, BV_CTA512, BV_TEAM_SPLIT, BV_TEAM64 };
+
+int launch_batched_variant(bool fp32, BatchArgs a, int v, int num_sms, cudaStream_t s) {
+  switch (v) {
+    case BV_TEAM_SPLIT:
+      a.team_split = 32;
+      return fp32 ? launch_batched_team(a, num_sms, s) : -1;
+    case BV_TEAM64:
+      a.team_split = 0;
+      return fp32 ? launch_batched_team(a, num_sms, s) : -1;
+    default: {
+      const int nt = v == BV_CTA128 ? 128 : v == BV_CTA256 ? 256 : 512;
+      return fp32 ? launch_batched<float>(a, nt, num_sms, s)
+                  : launch_batched<double>(a, nt, num_sms, s);
+    }
+  }
 }
 
 // Grow a device (pinned host when host == true) buffer to `need` elements.
@@ -700,7 +1172,7 @@ void batched_release(fram_ctx* c) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  void* dptr[] = {b->A, b->B, b->N, b->perm, b->desc, b->info, b->ptrs, b->queue};
+  void* dptr[] = {b->A, b->B, b->N, b->perm, b->desc, b->tdesc, b->info, b->ptrs, b->queue};
   for (void* p : dptr)
     if (p) cudaFree(p);
   void* hptr[] = {b->hA, b->hB, b->hN, b->hperm, b->hdesc, b->hinfo, b->hptrs};
@@ -834,26 +1306,58 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
   a.max_sweeps = p.max_sweeps;
   a.use_stall = fp32 ? 1 : 0;
 
-  // Autotuner: on the first batched call per precision, time each block size
-  // on a prefix of the batch (two waves of CTAs) and keep the fastest.
+  // Autotuner: on the first batched call per precision, time each kernel
+  // variant (block size of the CTA form; tile edge split of the team form)
+  // on a sample of the batch and keep the fastest.  The sample takes every
+  // stride-th pair of the queue, so it has the batch's length mix (a prefix
+  // would hold only the longest pairs), and up to 32 pairs per SM: with
+  // fewer, the last pairs' latency decides and favours the wider teams over
+  // the form with the higher throughput.  Each variant runs twice and its
+  // faster run counts.
   int& nt = S.tuned_nt[fp32 ? 1 : 0];
+  if (S.forced >= BV_TEAM_SPLIT && !fp32) {
+    set_err(c, "fram_solve_batched: the team kernel runs the mixed precisions only");
+    return FRAM_ERR_INVALID;
+  }
+  if (S.forced != 0) nt = S.forced;
   if (nt == 0) {
+    const int m = std::min(count, 32 * c->num_sms);
+    const int stride = count / m;
+    if (!grow(&S.tdesc, S.cap_tdesc, (size_t)m)) {
+      batched_release(c);
+      set_err(c, "batched buffers: allocation failed");
+      return FRAM_ERR_OOM;
+    }
+    std::vector<BatchDesc> sample(m);
+    for (int j = 0; j < m; ++j) sample[j] = desc[(size_t)j * stride];
+    BT_CUDA(cudaMemcpyAsync(S.tdesc, sample.data(), m * sizeof(BatchDesc),
+                            cudaMemcpyHostToDevice, s),
+            "copy tuning descriptors");
+    BT_CUDA(cudaStreamSynchronize(s), "synchronize");  // sample is a stack vector
     float best = 1e30f;
     BatchArgs t = a;
-    t.count = std::min(count, 4 * c->num_sms);
-    for (int cand : {128, 256, 512}) {
-      BT_CUDA(cudaMemsetAsync(S.queue, 0, 4, s), "memset");
-      BT_CUDA(cudaEventRecord(c->ev0, s), "event");
-      if (launch_batched_any(fp32, t, cand, c->num_sms, s) < 0)
-        return cuda_fail(c, cudaGetLastError(), "batched kernel");
-      BT_CUDA(cudaEventRecord(c->ev1, s), "event");
-      BT_CUDA(cudaEventSynchronize(c->ev1), "synchronize");
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-      c->launches += 1;
-      if (ms < best) {
-        best = ms;
-        nt = cand;
+    t.desc = S.tdesc;
+    t.count = m;
+    std::vector<int> cands = {BV_CTA128, BV_CTA256, BV_CTA512};
+    if (fp32) {
+      cands.push_back(BV_TEAM_SPLIT);
+      cands.push_back(BV_TEAM64);
+    }
+    for (int cand : cands) {
+      for (int rep = 0; rep < 2; ++rep) {
+        BT_CUDA(cudaMemsetAsync(S.queue, 0, 4, s), "memset");
+        BT_CUDA(cudaEventRecord(c->ev0, s), "event");
+        if (launch_batched_variant(fp32, t, cand, c->num_sms, s) < 0)
+          return cuda_fail(c, cudaGetLastError(), "batched kernel");
+        BT_CUDA(cudaEventRecord(c->ev1, s), "event");
+        BT_CUDA(cudaEventSynchronize(c->ev1), "synchronize");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->launches += 1;
+        if (ms < best) {
+          best = ms;
+          nt = cand;
+        }
       }
     }
   }
@@ -873,7 +1377,7 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
     BT_CUDA(cudaStreamBeginCapture(S.cap_stream, cudaStreamCaptureModeThreadLocal),
             "begin capture");
     cudaMemsetAsync(S.queue, 0, 4, S.cap_stream);
-    launch_batched_any(fp32, a, nt, c->num_sms, S.cap_stream);
+    launch_batched_variant(fp32, a, nt, c->num_sms, S.cap_stream);
     if (scatter)
       scatter_kernel<<<std::min(count, 2 * c->num_sms), 256, 0, S.cap_stream>>>(
           S.desc, count, S.N, S.perm,
@@ -936,6 +1440,28 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
 }
 
 }  // namespace fram
+
+extern "C" fram_status fram_set_batched_kernel(fram_ctx* c, int variant) {
+  using namespace fram;
+  if (!c) return FRAM_ERR_INVALID;
+  if (variant < 0 || variant > BV_TEAM64) {
+    set_err(c, "fram_set_batched_kernel: variant must be 0 (autotune) .. %d", (int)BV_TEAM64);
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->batched) c->batched = new BatchedState();
+  BatchedState& S = *static_cast<BatchedState*>(c->batched);
+  S.forced = variant;
+  S.tuned_nt[0] = S.tuned_nt[1] = 0;  // re-tune (or take the forced one) on the next call
+  return FRAM_OK;
+}
+
+extern "C" int fram_batched_kernel(const fram_ctx* c, int precision) {
+  using namespace fram;
+  if (!c || !c->batched) return 0;
+  const BatchedState& S = *static_cast<const BatchedState*>(c->batched);
+  return S.tuned_nt[precision != FRAM_PREC_FP64 ? 1 : 0];
+}
 
 extern "C" fram_status fram_solve_batched(fram_ctx* c, int count, const int* n,
                                           const double* const* A, const double* const* B,

@@ -190,3 +190,93 @@ def test_batched_full_keypoint_workload_sampled(torch_cuda, ctx):
     P64h = [p.cpu().numpy().astype(np.int64) for p in P64]
     Pmh = [p.cpu().numpy().astype(np.int64) for p in Pm]
     check_batch_equal_accuracy(pairs, Pmh, im, [(p, i.objective) for p, i in zip(P64h, i64)])
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+def test_batched_team_kernel_equal_accuracy(torch_cuda, ctx, variant):
+    # The team form (4: one warp for n <= 32, two warps above; 5: two warps
+    # for every pair) on the mixed batch: ER pairs one by one and the batch as
+    # a whole at equal accuracy with the oracle.
+    pairs = mixed_batch(3)
+    params = fr.fram_default_params(theta=10.0, precision=fr.FRAM_PREC_MIXED_BF16)
+    fr.fram_set_batched_kernel(ctx, variant)
+    try:
+        X, P, infos = run_batched(torch_cuda, ctx, pairs, params)
+        assert fr.fram_batched_kernel(ctx, fr.FRAM_PREC_MIXED_BF16) == variant
+    finally:
+        fr.fram_set_batched_kernel(ctx, 0)
+    refs = []
+    for g in pairs:
+        ref = o.fram(g.A, g.B, theta=10.0)
+        refs.append((ref.perm, ref.objective))
+    check_batch_equal_accuracy(pairs, P, infos, refs)
+
+
+@pytest.mark.parametrize("variant", [2, 4, 5])
+def test_batched_fp32_one_iteration_matches_oracle(torch_cuda, ctx, variant):
+    # One outer iteration of 10 sweeps in FP32, every form, at the tile-edge
+    # boundaries (n = 32 on one warp, 33 and 64 on two): N against the oracle's
+    # FP64 iteration.  FP32 products over n <= 64 terms (relative error below
+    # 64 u ~ 4e-6), then SDSN, which is non-expansive; N1 = 0.05 N0 + 0.95 D.
+    # The FP32 stop tolerance is set to the oracle's 1e-14, which 10 sweeps do
+    # not reach at theta = 2 for n >= 16, so both run exactly 10 sweeps.  At
+    # n = 10 the first sweep already lands on the doubly stochastic set (no
+    # entry is clipped), the oracle's gamma is at FP64 rounding and it stops
+    # after one sweep; FP32 cannot reach 1e-14 there and stops on its
+    # rounding-floor rule within a few sweeps instead, at the same fixed point.
+    torch = torch_cuda
+    params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_BF16, max_outer=1,
+                                    max_sweeps=10, polish_tol=1e-14)
+    pairs = [fi.gaussian_pair(n, jitter=0.02, seed=n) for n in (10, 16, 31, 32, 33, 48, 64)]
+    fr.fram_set_batched_kernel(ctx, variant)
+    try:
+        X, P, infos = run_batched(torch, ctx, pairs, params)
+    finally:
+        fr.fram_set_batched_kernel(ctx, 0)
+    for g, x, inf in zip(pairs, X, infos):
+        ref = o.fram(g.A, g.B, theta=2.0, max_outer=1, max_sweeps=10)
+        err = relF(x, ref.N)
+        print(f"variant={variant} n={g.n} relF(N1)={err:.2e}")
+        assert inf.outer_iters == 1
+        if ref.total_sweeps == 10:
+            assert inf.total_sweeps == 10
+        else:
+            assert ref.total_sweeps == 1 and 1 <= inf.total_sweeps <= 4, (g.n, inf.total_sweeps)
+        assert err <= 1e-4, (g.n, err)
+
+
+def test_batched_team_kernel_rejects_fp64(torch_cuda, ctx):
+    pairs = mixed_batch(1)[:3]
+    fr.fram_set_batched_kernel(ctx, 4)
+    try:
+        ns = [g.n for g in pairs]
+        st, _ = fr.fram_solve_batched(ctx, ns, [g.A for g in pairs], [g.B for g in pairs], None,
+                                      None, [np.empty(g.n, np.int32) for g in pairs], check=False)
+        assert st == fr.FRAM_ERR_INVALID
+    finally:
+        fr.fram_set_batched_kernel(ctx, 0)
+    st = fr.fram_set_batched_kernel(ctx, 9, check=False)
+    assert st == fr.FRAM_ERR_INVALID
+
+
+@pytest.mark.parametrize("variant", [2, 4])
+def test_batched_keypoint_workload_forms_agree(torch_cuda, ctx, variant):
+    # The full 4096-pair keypoint batch through a CTA form and the team form:
+    # each at equal accuracy (batch aggregate) with the FP64 batch.
+    torch = torch_cuda
+    pairs = fi.keypoint_batch(4096, seed=9)
+    ns = [g.n for g in pairs]
+    As = [torch.from_numpy(g.A).cuda() for g in pairs]
+    Bs = [torch.from_numpy(g.B).cuda() for g in pairs]
+    P64 = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    Pm = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    _, i64 = fr.fram_solve_batched(ctx, ns, As, Bs, fr.fram_default_params(theta=2.0), None, P64)
+    fr.fram_set_batched_kernel(ctx, variant)
+    try:
+        params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_BF16)
+        _, im = fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Pm)
+    finally:
+        fr.fram_set_batched_kernel(ctx, 0)
+    P64h = [p.cpu().numpy().astype(np.int64) for p in P64]
+    Pmh = [p.cpu().numpy().astype(np.int64) for p in Pm]
+    check_batch_equal_accuracy(pairs, Pmh, im, [(p, i.objective) for p, i in zip(P64h, i64)])
