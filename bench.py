@@ -808,6 +808,7 @@ def roofline(infos, n, precision, pk, src):
     dom["time_share"] = {"sdsn_ms": ms_sdsn, "gemm_ms": ms_gemm,
                          "polish_ms": sum(i.ms_polish for i in infos),
                          "update_ms": sum(i.ms_update for i in infos),
+                         "rounding_ms": sum(i.ms_rounding for i in infos),
                          "total_ms": sum(i.ms_total for i in infos)}
     other = dict(other)
     other["frac"] = other["achieved"] / other["peak"] if other["achieved"] and other["peak"] else None

@@ -120,6 +120,7 @@ typedef struct {
   double ms_sdsn;           /* device time in SDSN (step 6; FP32 phase if mixed)*/
   double ms_polish;         /* device time in the FP64 polish (mixed paths)     */
   double ms_update;         /* device time in the update + delta (steps 7-8)    */
+  double ms_rounding;       /* device time of the discretisation (eq. 2)        */
 } fram_info;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -186,7 +187,8 @@ fram_status fram_solve_batched(fram_ctx *ctx, int count, const int *n, const dou
 
 /* Kernel form of fram_solve_batched's persistent launch (an autotuning and
  * testing hook).  0 (default): on the first call per precision, time every
- * form on a prefix of the batch and keep the fastest.  1, 2, 3: one pair per
+ * form on a sample of the batch (every k-th pair, up to 32 per SM) and keep
+ * the fastest.  1, 2, 3: one pair per
  * CTA of 128, 256 or 512 threads (FP64 and mixed).  4: teams of two warps,
  * a pair with n <= 32 on one warp (tile edge 32), a larger one on both
  * (tile edge 64); 5: every pair on two warps (mixed precision only; an FP64
@@ -319,6 +321,25 @@ fram_status fram_sdsn_grouped(fram_ctx *ctx, int count, const int *n, const doub
  * W). */
 fram_status fram_assign(fram_ctx *ctx, int n, const double *W, int32_t *perm, double *value_out,
                         int *auction_phases_out);
+
+/* Concurrent searches of the assignment's exact completion (eq. 2) for
+ * n >= 1024, on `ctx` (fram_assign, the rounding of fram_solve and of served
+ * requests).  0 (default): 8.  1: one shortest-augmenting-path search at a
+ * time.  2..16: that many clusters of 8 CTAs, capped by how many can be
+ * resident; each searches from its own free row on a snapshot of the duals
+ * and commits its path under a lock, unless a commit since its start
+ * changed a column it popped, in which case it searches again.  Every
+ * setting returns an optimal permutation; only the choice among tied optima
+ * can differ from run to run.  FRAM_ERR_INVALID outside 0..16. */
+fram_status fram_set_lap_searches(fram_ctx *ctx, int searches);
+
+/* Statistics of the last assignment run by fram_assign or fram_solve on
+ * `ctx`: augmenting paths applied, searches repeated after a conflicting
+ * commit (always 0 for one search at a time) and Dijkstra steps of the last
+ * completion pass, repeated searches included.  Any pointer may be NULL.
+ * FRAM_ERR_INVALID if no assignment has run on ctx. */
+fram_status fram_lap_last_stats(const fram_ctx *ctx, int *augmented, int *repeats,
+                                long long *steps);
 
 /* Largest n that fram_sdsn_static accepts. */
 #define FRAM_SDSN_STATIC_MAX_N 4096

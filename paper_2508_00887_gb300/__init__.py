@@ -53,7 +53,7 @@ class FramInfo(C.Structure):
                 ("objective", C.c_double), ("match_error", C.c_double),
                 ("assignment_value", C.c_double), ("ms_total", C.c_double),
                 ("ms_gemm", C.c_double), ("ms_sdsn", C.c_double), ("ms_polish", C.c_double),
-                ("ms_update", C.c_double)]
+                ("ms_update", C.c_double), ("ms_rounding", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -104,6 +104,8 @@ def load(path: str | None = None):
         "fram_sdsn_f32": (i, [_P, i, _P, i, _P, i, d, d, i, C.POINTER(i), C.POINTER(d)]),
         "fram_sdsn_grouped": (i, [_P, i, _P, _P, _P, d, d, i, _P, _P]),
         "fram_assign": (i, [_P, i, _P, _P, C.POINTER(d), C.POINTER(i)]),
+        "fram_set_lap_searches": (i, [_P, i]),
+        "fram_lap_last_stats": (i, [_P, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_longlong)]),
         "fram_sdsn_static": (i, [i, _P, _P, d, d, i, _P, C.POINTER(i), C.POINTER(d), C.c_char_p,
                                  sz]),
     }
@@ -122,7 +124,7 @@ def exported_symbols():
             "fram_solve", "fram_solve_batched", "fram_set_batched_kernel", "fram_batched_kernel",
             "fram_submit",
             "fram_poll", "fram_serve_ticks", "fram_node_affinity", "fram_fra_exact", "fram_set_sparse_density", "fram_gradient", "fram_gradient_lowp", "fram_sdsn", "fram_sdsn_f32", "fram_sdsn_grouped",
-            "fram_assign", "fram_sdsn_static"]
+            "fram_assign", "fram_set_lap_searches", "fram_lap_last_stats", "fram_sdsn_static"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -348,6 +350,22 @@ def fram_fra_exact(ctx, n, X, D, theta, tol=1e-12, max_sweeps=10000, check=True)
     if check:
         _check(ctx, st)
     return st, sw.value, res.value
+
+
+def fram_set_lap_searches(ctx, searches, check=True):
+    st = load().fram_set_lap_searches(ctx, searches)
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def fram_lap_last_stats(ctx):
+    """(augmenting paths applied, searches repeated, Dijkstra steps) of the
+    last assignment."""
+    a, r, s = C.c_int(), C.c_int(), C.c_longlong()
+    st = load().fram_lap_last_stats(ctx, C.byref(a), C.byref(r), C.byref(s))
+    _check(ctx, st)
+    return a.value, r.value, s.value
 
 
 def fram_assign(ctx, n, W, perm, check=True, with_phases=False):

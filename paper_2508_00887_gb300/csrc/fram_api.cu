@@ -457,8 +457,10 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
   }
 
   // Alg. 1 step 10 and eq. 1 on the unscaled inputs.
+  FR_CUDA(cudaEventRecord(c->evp[0], c->stream), "event");
   FR_LAUNCH(launch_lap(w.N, ld, n, w.perm, &w.scal->lap, w.lap_ws, c->num_sms, c->wait_limit_ns,
-                       c->stream), "lap kernels");
+                       c->stream, c->lap_searches), "lap kernels");
+  FR_CUDA(cudaEventRecord(c->evp[1], c->stream), "event");
   FR_LAUNCH(launch_objective(A0, B0, K0, p.lambda, n, w.perm, &w.scal->obj, w.partials,
                              &w.scal->ticket_obj, c->stream),
             "objective kernel");
@@ -474,12 +476,14 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
           "readback");
   FR_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
   FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  c->lap_ran = true;
   if (w.hscal->lap.status != 0) {
     set_err(c, "assignment search did not terminate");
     return FRAM_ERR_TIMEOUT;
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  inf.ms_rounding = phase_ms(c, 0, 1);
   inf.lap_augmentations = w.hscal->lap.augmented;
   inf.lap_auction_phases = w.hscal->lap.auction_phases;
   inf.assignment_value = w.hscal->lap.value;
@@ -623,6 +627,27 @@ fram_status fram_solve(fram_ctx* c, int n, const double* A, const double* B, con
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "set device");
   std::lock_guard<std::mutex> lk(c->mu);
   return solve_one(c, n, A, B, K, p, X_out, perm_out, info);
+}
+
+fram_status fram_set_lap_searches(fram_ctx* c, int searches) {
+  if (!c) return FRAM_ERR_INVALID;
+  c->last_error.clear();
+  if (searches < 0 || searches > 16) {
+    set_err(c, "fram_set_lap_searches: searches must lie in 0..16");
+    return FRAM_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->lap_searches = searches;
+  return FRAM_OK;
+}
+
+fram_status fram_lap_last_stats(const fram_ctx* c, int* augmented, int* repeats,
+                                long long* steps) {
+  if (!c || !c->lap_ran || !c->ws.hscal) return FRAM_ERR_INVALID;
+  if (augmented) *augmented = c->ws.hscal->lap.augmented;
+  if (repeats) *repeats = c->ws.hscal->lap.repeats;
+  if (steps) *steps = c->ws.hscal->lap.steps;
+  return FRAM_OK;
 }
 
 fram_status fram_set_sparse_density(fram_ctx* c, double max_density) {
@@ -936,11 +961,12 @@ fram_status fram_assign(fram_ctx* c, int n, const double* W, int32_t* perm, doub
   FR_TRY(ensure_workspace(c, n));
   Workspace& w = c->ws;
   FR_LAUNCH(launch_lap(W, n, n, perm, &w.scal->lap, w.lap_ws, c->num_sms, c->wait_limit_ns,
-                       c->stream), "lap kernels");
+                       c->stream, c->lap_searches), "lap kernels");
   FR_CUDA(cudaMemcpyAsync(&w.hscal->lap, &w.scal->lap, sizeof(LapStats), cudaMemcpyDeviceToHost,
                           c->stream),
           "readback");
   FR_CUDA(cudaStreamSynchronize(c->stream), "synchronize");
+  c->lap_ran = true;
   if (w.hscal->lap.status != 0) {
     set_err(c, "assignment search did not terminate");
     return FRAM_ERR_TIMEOUT;

@@ -67,6 +67,8 @@ struct fram_ctx {
   std::atomic<uint64_t> launches{0};
   uint64_t wait_limit_ns = fram::kWaitLimitNs;
   double sparse_density = 0.2;  // FP64 gradient uses CSR up to this fraction of nonzeros
+  int lap_searches = 0;         // concurrent LAP searches (0 = default, 1 = sequential)
+  bool lap_ran = false;         // an assignment has run (fram_lap_last_stats)
   std::mutex mu;        // serialises the synchronous entry points
   std::mutex serve_mu;  // guards creation of the serving scheduler
   fram::Workspace ws;

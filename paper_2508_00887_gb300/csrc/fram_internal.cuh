@@ -203,8 +203,9 @@ struct LapStats {
   int augmented;       // augmenting paths of the exact completion
   int status;          // 0 ok, 1 the search did not terminate
   int auction_phases;  // epsilon-scaling phases completed, -1 if the auction did not run
-  int pad;
+  int repeats;         // concurrent completion: searches repeated after a conflicting commit
   double value;
+  long long steps;     // Dijkstra steps of the last completion pass, repeated searches included
 };
 
 struct ObjStats {
@@ -293,8 +294,10 @@ int launch_update(double* N, int ldn, const double* D, int ldd, int n, double al
                   IterStats* st, double* partials, unsigned* ticket, cudaStream_t s);
 size_t update_partials_elems(int n);
 
+// searches: concurrent searches of the cluster completion (n >= 1024);
+// 0 = the default, 1 = one search at a time.
 int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
-               int num_sms, uint64_t limit_ns, cudaStream_t s);
+               int num_sms, uint64_t limit_ns, cudaStream_t s, int searches = 0);
 size_t lap_workspace_bytes(int n);
 
 int launch_wait_selftest(GridBarrier* bar, int* status, int blocks, uint64_t limit_ns,

@@ -43,6 +43,18 @@ constexpr int kQuantBits = 36;   // price quantum = (max W - min W) * 2^-36
 constexpr int kPriceBits = 44;   // quantised prices < 2^44 (256x the value range)
 constexpr int kPhases = 12;      // epsilon = range * 4^-phase, phase = 1..12
 
+// Concurrent completion (lap_solve_conc_kernel), one per pass.
+struct ConcCtl {
+  int lock;          // 0 free, 1 held by a committing cluster
+  unsigned seq;      // commits published so far (release store)
+  int next_row;      // work queue over the rows
+  int commits;       // augmenting paths applied
+  int aborts;        // searches repeated after a conflicting commit
+  int err;           // 1: a search did not terminate or a wait expired
+  long long steps;   // Dijkstra steps of every search, repeated ones included
+  long long applied_steps;  // steps of the applied searches (the step budget)
+};
+
 struct LapCtl {
   GridBarrier bar;
   unsigned long long wmax_key;  // ordered keys of max / min over W
@@ -52,6 +64,7 @@ struct LapCtl {
   int phases;                   // auction phases completed
   int status;                   // DEV_TIMEOUT if an auction wait expired
   int need_auction;             // the first completion ran out of its step budget
+  ConcCtl cc[2];                // concurrent completion, by pass
 };
 
 struct LapWs {
@@ -61,6 +74,7 @@ struct LapWs {
   int* rowcol;     // [n] column matched to row i, -1 if free
   int* way;        // [n] completion: row that reached column j
   int* cand;       // [n] candidate column of row i from step 1 or 2, -1 if none
+  unsigned* cseq;  // [n] concurrent completion: last commit that changed column j
   double* rowmax;  // [n]
   double* u;       // [n] row potentials of the kept pairs
   double* v;       // [n] column potentials
@@ -77,7 +91,8 @@ __host__ __device__ inline LapWs carve(void* base, int n) {
   LapWs w;
   char* p = static_cast<char*>(base);
   const size_t ib = al256((size_t)n * sizeof(int)), db = al256((size_t)n * sizeof(double));
-  int** ia[] = {&w.argc, &w.owner, &w.colrow, &w.rowcol, &w.way, &w.cand};
+  int** ia[] = {&w.argc, &w.owner, &w.colrow, &w.rowcol, &w.way, &w.cand,
+                reinterpret_cast<int**>(&w.cseq)};
   for (int** q : ia) {
     *q = reinterpret_cast<int*>(p);
     p += ib;
@@ -324,6 +339,7 @@ __global__ void lap_candidates_kernel(LapWs w, int n, int pass) {
   const double dq = w.ctl->dq;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     w.colrow[j] = -1;
+    w.cseq[j] = 0u;
     if (auction) {
       const unsigned long long k = w.key[j];
       w.v[j] = -(double)(k >> kOwnerBits) * dq;
@@ -357,6 +373,7 @@ __global__ void lap_duals_kernel(const double* __restrict__ W, int ldw, int n, L
       if (j >= 0 && row[j] + w.v[j] == best) {
         w.rowcol[i] = j;
         w.colrow[j] = i;
+        w.wmat[j] = row[j];  // the concurrent completion reads W[colrow[j]][j] here
       } else {
         w.rowcol[i] = -1;
       }
@@ -493,6 +510,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
   if (tid == 0) {
     s_aug = 0;
     st->status = 0;
+    st->repeats = 0;
     st->auction_phases = pass == 1 && auction_on(w.ctl) ? w.ctl->phases : -1;
   }
   __syncthreads();
@@ -623,6 +641,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
     }
     __syncthreads();
   }
+  if (tid == 0) st->steps = total;
 
   double val = 0.0;
   for (int i = tid; i < n; i += kLapThreads) {
@@ -690,9 +709,10 @@ __device__ __forceinline__ ColState col_state(unsigned char* sm, int S) {
 }
 
 // First relaxation from the free row f: labels -(W_fj + v_j) for this CTA's
-// columns [jb, jb + ns) and this thread's best (label key, tie key).
+// columns [jb, jb + ns) and this thread's best (label key, tie key).  predl
+// holds the predecessor rows of this CTA's columns (local index).
 __device__ __forceinline__ void relax_first(const double* __restrict__ rowf, int f, int n, int jb,
-                                            int ns, const ColState& c, int* pred,
+                                            int ns, const ColState& c, int* predl,
                                             unsigned long long& best, int& bk) {
   best = kVisited;
   bk = 0x7fffffff;
@@ -702,7 +722,7 @@ __device__ __forceinline__ void relax_first(const double* __restrict__ rowf, int
     const unsigned long long dk = okey(-(x + c.v[jl]));
     c.dkey[jl] = dk;
     c.tkey[jl] = okey(x);
-    pred[j] = f;
+    predl[jl] = f;
     const int kk = c.colrow[jl] == -1 ? j : j + n;
     if (dk < best || (dk == best && kk < bk)) {
       best = dk;
@@ -714,7 +734,7 @@ __device__ __forceinline__ void relax_first(const double* __restrict__ rowf, int
 // One Dijkstra step's relaxation with row i (shift h) over this CTA's
 // unvisited columns, and this thread's best candidate afterwards.
 __device__ __forceinline__ void relax_row(const double* __restrict__ rowi, double h, int i, int n,
-                                          int jb, int ns, const ColState& c, int* pred,
+                                          int jb, int ns, const ColState& c, int* predl,
                                           unsigned long long& best, int& bk) {
   const int tid = threadIdx.x;
   double wv[kSolveUnroll];
@@ -750,7 +770,7 @@ __device__ __forceinline__ void relax_row(const double* __restrict__ rowi, doubl
         if (nk < dk) {
           dk = nk;
           c.dkey[jl] = nk;
-          pred[jb + jl] = i;
+          predl[jl] = i;
         }
       }
       const int kk = c.colrow[jl] == -1 ? jb + jl : jb + jl + n;
@@ -844,6 +864,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     s_aug = 0;
     if (cr == 0) {
       st->status = 0;
+      st->repeats = 0;
       st->auction_phases = pass == 1 && auction_on(w.ctl) ? w.ctl->phases : -1;
     }
   }
@@ -855,7 +876,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     if (w.rowcol[f] != -1) continue;  // uniform: written before the last cluster barrier
     unsigned long long best;
     int bk;
-    relax_first(W + (size_t)f * ldw, f, n, jb, ns, c, pred, best, bk);
+    relax_first(W + (size_t)f * ldw, f, n, jb, ns, c, pred + jb, best, bk);
     CandSlot win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
     double mu = okey_value(win.key);
     int steps = 0, j1;
@@ -871,7 +892,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
         c.dkey[j1 - jb] = kVisited;
       }
       if (win.i == -1) break;  // j1 is free: augment
-      relax_row(W + (size_t)win.i * ldw, win.h, win.i, n, jb, ns, c, pred, best, bk);
+      relax_row(W + (size_t)win.i * ldw, win.h, win.i, n, jb, ns, c, pred + jb, best, bk);
       win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
       mu = okey_value(win.key);
       ++total;
@@ -910,6 +931,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
   }
 
   if (cr != 0) return;
+  if (tid == 0) st->steps = total;
   double val = 0.0;
   for (int r = tid; r < n; r += kClusterThreads) {
     const int j = w.rowcol[r];
@@ -926,6 +948,288 @@ __global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_cluster_kernel(
     if (lane == 0) {
       st->value = t;
       st->augmented = s_aug;
+    }
+  }
+}
+
+// Concurrent completion: K clusters of kLapCluster CTAs, each running the
+// search above from its own free row, with optimistic commits.
+//
+// A search reads the shared state (v, colrow and W[colrow[j]][j] in L2)
+// into its shared memory at its start, after reading the number of
+// published commits s0 with acquire semantics.  When it reaches a free
+// column it takes a lock and checks every column it popped: if a commit
+// numbered above s0 changed that column, the search is repeated from the
+// same row on fresh state; otherwise it applies its potentials and its path
+// flip, stamps every popped column with its own commit number and publishes
+// that number with a release store.  Commits change only the columns their
+// own search popped: they lower v_j there (v_j += d_j - mu with d_j <= mu),
+// which can only raise the labels another search sees for those columns,
+// and reassign the rows of the path, which are the rows of popped columns.
+// A search none of whose popped columns was changed since s0 therefore pops
+// the same columns in the same order on the current state as on its
+// snapshot (stale or torn reads touch only columns it did not pop, or are
+// caught by the check).  The applied searches are a sequence of exact
+// shortest augmenting paths from feasible duals, the Hungarian method run in
+// another order, so the assignment is optimal; between tied optima the
+// choice may differ from run to run.
+//
+// Every branch and barrier is uniform inside a cluster: the row, s0, the
+// stop flag and the lock outcome come from CTA 0's shared memory, the
+// validation result from every CTA's flag, the pops from the exchange.
+// Clusters never wait on one another except for the lock, whose holder is
+// running its (wait-free) commit; the wait on it is bounded by limit_ns.
+constexpr int kMaxSearches = 16;
+constexpr int kDefaultSearches = 8;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_gpu_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct ConcJob {
+  int f;        // free row of this search
+  unsigned s0;  // commits published when it started
+  int stop;     // leave: no row left, an error, or (pass 0) the budget is spent
+  int ok;       // the lock was taken
+  unsigned seq; // commits published when the lock was taken
+};
+
+__global__ void __launch_bounds__(kClusterThreads, 1) lap_solve_conc_kernel(
+    const double* __restrict__ W, int ldw, int n, LapWs w, int pass, long long budget,
+    uint64_t limit_ns) {
+  if (pass == 1 && !ld_volatile_s32(&w.ctl->need_auction)) return;  // uniform (earlier kernel)
+  cg::cluster_group cl = cg::this_cluster();
+  const int cr = (int)cl.block_rank();
+  const int S = (n + kLapCluster - 1) / kLapCluster;
+  const int jb = min(n, cr * S), ns = min(n, jb + S) - jb;
+  extern __shared__ __align__(16) unsigned char lap_sm[];
+  const ColState c = col_state(lap_sm, S);
+  int* predl = c.colrow + S;
+  __shared__ CandSlot slots[2][kClusterWarps];
+  __shared__ CandSlot s_win;
+  __shared__ ConcJob s_job;
+  __shared__ int s_conf;
+  __shared__ int s_rows[32];   // CTA 0: free rows taken from the queue, not yet searched
+  __shared__ int s_nrows, s_rpos;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) s_nrows = s_rpos = 0;
+  ConcCtl* cc = &w.ctl->cc[pass];
+  const ConcJob* job0 = cl.map_shared_rank(&s_job, 0);
+  int par = 0;
+  int f = -1;
+  bool retry = false;
+  while (true) {
+    // Next row (or the same one again), and s0.  Warp 0 of CTA 0 takes 32
+    // rows of the queue per atomic and keeps the free ones (rows are only
+    // ever assigned by their own search, so "free" cannot go stale).
+    if (cr == 0 && tid < 32) {
+      int stop = 0;
+      if (lane == 0)
+        stop = ld_volatile_s32(&cc->err) != 0 ||
+               (pass == 0 && ld_volatile_s32(&w.ctl->need_auction) != 0);
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      int row = f;
+      if (!stop && !retry) {
+        row = n;
+        for (int chunk = 0; chunk < n / 32 + 3; ++chunk) {  // ceil(n / 32) refills at most
+          __syncwarp();
+          if (s_rpos < s_nrows) {
+            row = s_rows[s_rpos];
+            break;
+          }
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&cc->next_row, 32);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= n) break;
+          const int r = base + lane;
+          const bool fr = r < n && __ldcg(&w.rowcol[r]) == -1;
+          const unsigned m = __ballot_sync(0xffffffffu, fr);
+          if (fr) s_rows[__popc(m & ((1u << lane) - 1u))] = r;
+          __syncwarp();
+          if (lane == 0) {
+            s_nrows = __popc(m);
+            s_rpos = 0;
+          }
+        }
+        __syncwarp();
+        if (lane == 0 && row < n) ++s_rpos;
+      }
+      if (lane == 0) {
+        ConcJob j{};
+        j.stop = stop || row >= n;
+        j.f = row;
+        j.s0 = ld_acquire_gpu_u32(&cc->seq);
+        s_job = j;
+      }
+    }
+    cl.sync();
+    const int stop = job0->stop;
+    f = job0->f;
+    const unsigned s0 = job0->s0;
+    if (stop) {
+      cl.sync();  // no CTA leaves while another may still read its shared memory
+      return;
+    }
+    // Snapshot of this CTA's columns, then the first relaxation from f.
+    for (int jl = tid; jl < ns; jl += kClusterThreads) {
+      c.v[jl] = __ldcg(&w.v[jb + jl]);
+      c.colrow[jl] = __ldcg(&w.colrow[jb + jl]);
+      c.wmat[jl] = __ldcg(&w.wmat[jb + jl]);
+    }
+    __syncthreads();  // the exchange reads other threads' snapshot entries
+    unsigned long long best;
+    int bk;
+    relax_first(W + (size_t)f * ldw, f, n, jb, ns, c, predl, best, bk);
+    CandSlot win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
+    double mu = okey_value(win.key);
+    int steps = 0, j1;
+    bool failed = false;
+    while (true) {
+      if (win.k < 0 || win.k >= 2 * n || win.key == kVisited) {  // no finite label left
+        failed = true;
+        break;
+      }
+      j1 = win.k >= n ? win.k - n : win.k;
+      if (j1 >= jb && j1 < jb + ns && (j1 - jb) % kClusterThreads == tid) {
+        c.tkey[j1 - jb] = (unsigned long long)__double_as_longlong(mu);
+        c.dkey[j1 - jb] = kVisited;
+      }
+      if (win.i == -1) break;  // j1 is free: commit
+      relax_row(W + (size_t)win.i * ldw, win.h, win.i, n, jb, ns, c, predl, best, bk);
+      win = cluster_exchange(cl, cr, n, jb, c, slots, &s_win, par, best, bk);
+      mu = okey_value(win.key);
+      if (++steps > n) {
+        failed = true;
+        break;
+      }
+    }
+    if (failed) {
+      if (cr == 0 && tid == 0) atomicExch(&cc->err, 1);
+      cl.sync();
+      return;
+    }
+    // Lock (bounded wait), then every CTA checks its popped columns.
+    if (cr == 0 && tid == 0) {
+      const uint64_t t0 = globaltimer_ns();
+      int ok = 1;
+      while (atomicCAS(&cc->lock, 0, 1) != 0) {
+        if (globaltimer_ns() - t0 > limit_ns) {
+          ok = 0;
+          atomicExch(&cc->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();  // acquire: the holders' writes before their release
+      s_job.ok = ok;
+      s_job.seq = ok ? ld_acquire_gpu_u32(&cc->seq) : 0u;
+    }
+    cl.sync();
+    if (!job0->ok) {
+      cl.sync();
+      return;
+    }
+    const unsigned seq = job0->seq;
+    int conf = 0;
+    for (int jl = tid; jl < ns; jl += kClusterThreads)
+      if (c.dkey[jl] == kVisited && __ldcg(&w.cseq[jb + jl]) > s0) conf = 1;
+    conf = __syncthreads_or(conf);
+    if (tid == 0) s_conf = conf;
+    cl.sync();
+    int any = tid < kLapCluster ? *cl.map_shared_rank(&s_conf, tid) : 0;
+    any = __syncthreads_or(any);
+    if (any) {
+      if (cr == 0 && tid == 0) {
+        atomicAdd(&cc->aborts, 1);
+        atomicAdd((unsigned long long*)&cc->steps, (unsigned long long)steps);
+        st_release_gpu_s32(&cc->lock, 0);
+      }
+      retry = true;
+      continue;  // the next cl.sync orders the flag reads before s_conf is written again
+    }
+    // Apply: potentials and stamps of the popped columns, then (CTA 0) the
+    // path flip, the publication of commit seq + 1 and the unlock.
+    const unsigned mine = seq + 1;
+    for (int jl = tid; jl < ns; jl += kClusterThreads)
+      if (c.dkey[jl] == kVisited) {
+        w.v[jb + jl] = c.v[jl] + __longlong_as_double((long long)c.tkey[jl]) - mu;
+        w.cseq[jb + jl] = mine;
+      }
+    __threadfence();
+    cl.sync();  // every CTA's writes are done; pred is final
+    if (cr == 0 && tid == 0) {
+      int j = j1;
+      for (int hop = 0; hop <= n; ++hop) {
+        const int owner = j / S;
+        const int r = *cl.map_shared_rank(predl + (j - owner * S), owner);
+        const int prev = r >= 0 && r < n ? __ldcg(&w.rowcol[r]) : -1;
+        if (r < 0 || r >= n || (r != f && (prev < 0 || prev >= n))) {  // never on valid state
+          atomicExch(&cc->err, 1);
+          break;
+        }
+        w.colrow[j] = r;
+        w.wmat[j] = W[(size_t)r * ldw + j];
+        w.rowcol[r] = j;
+        w.cseq[j] = mine;
+        if (r == f) break;
+        j = prev;
+      }
+      __threadfence();
+      st_release_gpu_u32(&cc->seq, mine);
+      atomicAdd(&cc->commits, 1);
+      atomicAdd((unsigned long long*)&cc->steps, (unsigned long long)steps);
+      // The budget counts the applied searches only: they are the work one
+      // search at a time would do (repeated searches are the price of
+      // concurrency, not a sign of a hard instance).
+      const long long tot = atomicAdd((unsigned long long*)&cc->applied_steps,
+                                      (unsigned long long)steps) + steps;
+      if (pass == 0 && budget > 0 && tot > budget) atomicExch(&w.ctl->need_auction, 1);
+      st_release_gpu_s32(&cc->lock, 0);
+    }
+    retry = false;
+    cl.sync();  // the flip has read every CTA's pred before the next search writes it
+  }
+}
+
+// Result of the concurrent completion: perm, the assignment value and the
+// statistics of the pass that ran last.
+__global__ void lap_conc_finish_kernel(const double* __restrict__ W, int ldw, int n, LapWs w,
+                                       int32_t* __restrict__ perm, LapStats* st) {
+  const int pass = ld_volatile_s32(&w.ctl->need_auction) ? 1 : 0;
+  const ConcCtl& cc = w.ctl->cc[pass];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double val = 0.0;
+  int unplaced = 0;
+  for (int r = tid; r < n; r += blockDim.x) {
+    const int j = w.rowcol[r];
+    perm[r] = j;
+    if (j >= 0)
+      val += W[(size_t)r * ldw + j];
+    else
+      unplaced = 1;
+  }
+  val = warp_sum(val);
+  __shared__ double rsum[32];
+  if (lane == 0) rsum[warp] = val;
+  unplaced = __syncthreads_or(unplaced);
+  if (warp == 0) {
+    double t = lane < (int)(blockDim.x >> 5) ? rsum[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) {
+      st->value = t;
+      st->augmented = cc.commits;
+      st->status = (cc.err != 0 || unplaced) ? 1 : 0;
+      st->auction_phases = pass == 1 && auction_on(w.ctl) ? w.ctl->phases : -1;
+      st->repeats = cc.aborts;
+      st->steps = cc.steps;
     }
   }
 }
@@ -994,15 +1298,48 @@ bool cluster_ok(size_t smem) {
   return clusters >= 1;
 }
 
+// Concurrent completion: how many clusters of kLapCluster CTAs with `smem`
+// bytes each can be resident together, capped at `want`.
+int conc_clusters(size_t smem, int want) {
+  static DeviceCache attr;
+  if (device_cached(attr, [] {
+        if (cudaFuncSetAttribute(lap_solve_conc_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSolveSmemCap) != cudaSuccess) {
+          cudaGetLastError();
+          return -1;
+        }
+        return 1;
+      }) < 0)
+    return 0;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kLapCluster * want);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kLapCluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, lap_solve_conc_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return clusters < want ? clusters : want;
+}
+
 }  // namespace
 
 size_t lap_workspace_bytes(int n) {
-  return 6 * al256((size_t)n * sizeof(int)) + 6 * al256((size_t)n * sizeof(double)) +
+  return 7 * al256((size_t)n * sizeof(int)) + 6 * al256((size_t)n * sizeof(double)) +
          al256(sizeof(LapCtl));
 }
 
 int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, void* ws,
-               int num_sms, uint64_t limit_ns, cudaStream_t s) {
+               int num_sms, uint64_t limit_ns, cudaStream_t s, int searches) {
   LapWs w = carve(ws, n);
   // The auction key holds a 20-bit row index; beyond that the first
   // completion runs without a budget.
@@ -1029,7 +1366,30 @@ int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, voi
   const int S = (n + kLapCluster - 1) / kLapCluster;
   const size_t csm = (size_t)S * (4 * sizeof(double) + sizeof(int));
   const bool use_cluster = n >= 1024 && csm <= kSolveSmemCap && cluster_ok(csm);
+  // Concurrent searches (K clusters) unless one is asked for; they add pred
+  // (4 bytes per column) to the per-CTA state.
+  const size_t qsm = csm + (size_t)S * sizeof(int);
+  int K = searches > 0 ? searches : kDefaultSearches;
+  if (K > kMaxSearches) K = kMaxSearches;
+  if (use_cluster && K > 1 && qsm <= kSolveSmemCap) K = conc_clusters(qsm, K);
+  const bool use_conc = use_cluster && K > 1 && qsm <= kSolveSmemCap;
   auto solve = [&](int pass, long long bud) -> bool {
+    if (use_conc) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(kLapCluster * K);
+      cfg.blockDim = dim3(kClusterThreads);
+      cfg.dynamicSmemBytes = qsm;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kLapCluster;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, lap_solve_conc_kernel, W, ldw, n, w, pass, bud,
+                                limit_ns) == cudaSuccess;
+    }
     if (use_cluster) {
       cudaLaunchConfig_t cfg{};
       cfg.gridDim = dim3(kLapCluster);
@@ -1068,6 +1428,10 @@ int launch_lap(const double* W, int ldw, int n, int32_t* perm, LapStats* st, voi
     lap_duals_kernel<<<rblocks, 256, 0, s>>>(W, ldw, n, w, 1);
     if (!solve(1, 0)) return -1;
     launches += 4;
+  }
+  if (use_conc) {
+    lap_conc_finish_kernel<<<1, 256, 0, s>>>(W, ldw, n, w, perm, st);
+    launches += 1;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
 }

@@ -484,7 +484,7 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       r->Nres.resize((size_t)r->n * r->n);
       r->permres.resize(r->n);
       SV_OK(launch_lap(r->N, r->ld, r->n, r->perm, &st->lap, r->lap_ws, c->num_sms,
-                       c->wait_limit_ns, s));
+                       c->wait_limit_ns, s, c->lap_searches));
       SV_OK(launch_objective(r->A0, r->B0, nullptr, r->p.lambda, r->n, r->perm, &st->obj, r->upart,
                              &st->ticket_obj, s));
       cudaMemcpy2DAsync(r->Nres.data(), (size_t)r->n * 8, r->N, (size_t)r->ld * 8, (size_t)r->n * 8,

@@ -74,7 +74,7 @@ int main(void) {{
     ("fram_info", fr.FramInfo,
      ["outer_iters", "total_sweeps", "polish_sweeps", "sdsn_converged_last", "lap_augmentations",
       "lap_auction_phases", "delta", "gamma", "objective", "match_error", "assignment_value", "ms_total",
-      "ms_gemm", "ms_sdsn", "ms_polish", "ms_update"]),
+      "ms_gemm", "ms_sdsn", "ms_polish", "ms_update", "ms_rounding"]),
 ])
 def test_struct_layouts_match_header(cname, pystruct, cfields):
     size, offs = _c_layout(cname, cfields)
