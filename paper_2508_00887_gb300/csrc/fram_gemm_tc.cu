@@ -9,7 +9,8 @@
 // accumulation is FP32 in tensor memory.
 //
 // Persistent, warp-specialised: one CTA per SM walks its share of the
-// 128 x BN output tiles (BN = 256 for large ld, else 128) in a grouped order
+// 128 x BN output tiles (BN = 256 for large ld; 64 where 128 x 128 tiles
+// would leave SMs idle, ld <= 1536; else 128) in a grouped order
 // (8 row panels at a time, so concurrent CTAs share A and B strips in L2):
 //   warp 0     TMA producer: 128-byte-swizzled A/B k-slices into a 4-stage
 //              shared-memory ring (mbarrier full/empty pairs)
@@ -723,9 +724,13 @@ int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int k
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bop) |
        reinterpret_cast<uintptr_t>(C)) & 15)
     return -1;
-  // 256-wide tiles once every CTA gets at least two of them.
-  const bool wide = (ld / BM) * ((ld + 255) / 256) >= 2 * num_sms_cached();
-  const int bn = wide ? 256 : 128;
+  // 256-wide tiles once every CTA gets at least two of them; 64-wide ones
+  // while 128-wide tiles would not give every SM one (twice the tiles, each
+  // CTA streaming a narrower B strip).
+  const int sms = num_sms_cached();
+  const bool wide = (ld / BM) * ((ld + 255) / 256) >= 2 * sms;
+  const bool narrow = !wide && (ld / BM) * ((ld + 127) / 128) < sms;
+  const int bn = wide ? 256 : (narrow ? 64 : 128);
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, ld, kind, BM) || !make_map(&mb, Bop, ld, kind, bn)) return -1;
   GemmArgs g{};
@@ -739,8 +744,12 @@ int launch_gemm_tc(const void* A, const void* Bop, void* C, int ld, int n, int k
   g.cmax = cmax;
   g.err = err;
   g.limit_ns = limit_ns;
-  if (kind == 0) return wide ? launch_k<0, 256>(ma, mb, g, ld, s) : launch_k<0, 128>(ma, mb, g, ld, s);
-  return wide ? launch_k<1, 256>(ma, mb, g, ld, s) : launch_k<1, 128>(ma, mb, g, ld, s);
+  if (kind == 0) {
+    if (wide) return launch_k<0, 256>(ma, mb, g, ld, s);
+    return narrow ? launch_k<0, 64>(ma, mb, g, ld, s) : launch_k<0, 128>(ma, mb, g, ld, s);
+  }
+  if (wide) return launch_k<1, 256>(ma, mb, g, ld, s);
+  return narrow ? launch_k<1, 64>(ma, mb, g, ld, s) : launch_k<1, 128>(ma, mb, g, ld, s);
 }
 
 }  // namespace fram

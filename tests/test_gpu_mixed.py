@@ -52,8 +52,10 @@ def round_tf32(x):
 
 
 @pytest.mark.parametrize("precision", [fr.FRAM_PREC_MIXED_BF16, fr.FRAM_PREC_MIXED_TF32])
-@pytest.mark.parametrize("n", [50, 128, 200, 300, 1000])
+@pytest.mark.parametrize("n", [50, 128, 200, 300, 1000, 1500, 2048])
 def test_gradient_lowp_matches_emulation(torch_cuda, ctx, precision, n):
+    # Tile shapes: 128 x 64 up to ld = 1536 (n = 50 .. 1500), 128 x 128 at
+    # ld = 2048.
     torch = torch_cuda
     rng = np.random.default_rng(n + 10 * precision)
     A = rng.random((n, n)); A = 0.5 * (A + A.T)
@@ -68,8 +70,12 @@ def test_gradient_lowp_matches_emulation(torch_cuda, ctx, precision, n):
     fr.fram_gradient_lowp(ctx, n, dev(A), dev(N), dev(B), X, precision, dev(K), 0.5)
     Xg = X.cpu().numpy().astype(np.float64)
     # FP32 accumulation over n terms; T is re-rounded, so allow a few ulps of
-    # the input format where a rounding boundary of T falls differently.
-    tol = 2e-5 if precision == fr.FRAM_PREC_MIXED_TF32 else 4e-4
+    # the input format where a rounding boundary of T falls differently.  The
+    # tensor cores' FP32 accumulation also drops low-order bits on each add:
+    # a bias toward zero that grows linearly with the number of terms
+    # (measured 2.0e-5 relative at n = 1500 and 2.7e-5 at n = 2048, about
+    # 1.3e-8 n), so the TF32 bound grows with n, 1.5x above those values.
+    tol = 2e-5 * max(1.0, n / 1000) if precision == fr.FRAM_PREC_MIXED_TF32 else 4e-4
     assert relF(Xg, ref) < tol
     exact = A @ N @ B + 0.5 * K
     assert relF(Xg, exact) < (2e-3 if precision == fr.FRAM_PREC_MIXED_TF32 else 1e-2)
