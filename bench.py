@@ -380,6 +380,7 @@ def run_batch(args):
     Ah = [torch.from_numpy(g.A).pin_memory().numpy() for g in pairs]
     Bh = [torch.from_numpy(g.B).pin_memory().numpy() for g in pairs]
     Ph = [np.empty(g.n, dtype=np.int32) for g in pairs]
+    fr.fram_solve_batched(ctx, ns, Ah, Bh, params, None, Ph)  # untimed: re-tunes after the reset
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
@@ -754,7 +755,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     """DRAM bytes per FP32 SDSN launch (dram__bytes_read.sum +
     dram__bytes_write.sum, one ncu capture of the current kernel), or None
     where no capture covers the size:
-      n = 1000: 4.16 MB per launch, whatever the sweep count: the tiles stay
+      n = 1000: 4.17 MB per launch, whatever the sweep count: the tiles stay
         in shared memory and only X is read (capture of this workload);
       n >= 6144 (the matrix far above L2): 7.80 bytes per element per pass,
         measured at n = 6144 (59.16 GB over 201 passes of 6144^2), scaled to
@@ -762,7 +763,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     if s != 4:
         return None
     if n == 1000:
-        return 4.16e6
+        return 4.17e6
     if n >= 6144:
         return 7.80 * n * n * (sweeps_per_launch + 1.0)
     return None
@@ -788,6 +789,26 @@ def roofline(infos, n, precision, pk, src):
             "peak": pk.get("hbm_gbs"), "unit": "GB/s",
             "per_launch_us": 1e3 * ms_sdsn / max(launches, 1),
             "per_sweep_us": 1e3 * ms_sdsn / max(sweeps, 1)}
+    if s == 4 and 96 < n <= 1024:
+        # The FP32 iterate stays on chip in one thread-block cluster (DRAM
+        # carries X once), so the sweep is bound by its arithmetic and
+        # exchange on the cluster's SMs, not by HBM: 5 n^2 FP32 operations
+        # per sweep (y + a_i, - b_j, the clamp, the row and the column
+        # accumulation) against one operation per lane per clock.
+        side = 1 if n <= 256 else (2 if n <= 512 else 4)
+        tc = ((-(-n // side)) + 3) // 4 * 4
+        sms = side * side
+        clock_ghz = 2.07
+        ops = 5.0 * n * n * sweeps
+        sdsn = {"kernel": f"sdsn_cluster_kernel<{'1, 16' if tc <= 128 else '2, 8'}>",
+                "bound": "alu",
+                "achieved": ops / (ms_sdsn / 1e3) / 1e12 if ms_sdsn else None,
+                "peak": sms * 128 * clock_ghz / 1e3, "unit": "TFLOP/s",
+                "peak_source": f"derived: the cluster's {sms} SMs x 128 FP32 lanes x 1 operation "
+                               f"per clock x {clock_ghz} GHz (adds and max, no FMA)",
+                "gpu_peak": 152 * 128 * clock_ghz / 1e3,
+                "per_launch_us": 1e3 * ms_sdsn / max(launches, 1),
+                "per_sweep_us": 1e3 * ms_sdsn / max(sweeps, 1)}
     if precision == "fp64":
         peak_t, unit_peak = 1.25, "TFLOP/s (nominal FP64, no measured FP64 peak)"
     elif precision == "bf16":
@@ -804,6 +825,8 @@ def roofline(infos, n, precision, pk, src):
     dom, other = (sdsn, gemm) if ms_sdsn >= ms_gemm else (gemm, sdsn)
     dom = dict(dom)
     dom["frac"] = dom["achieved"] / dom["peak"] if dom["achieved"] and dom["peak"] else None
+    if dom.get("gpu_peak") and dom["achieved"]:
+        dom["gpu_frac"] = dom["achieved"] / dom["gpu_peak"]
     dom["peak_source"] = dom.get("peak_source", f"{src} hbm_gbs")
     dom["time_share"] = {"sdsn_ms": ms_sdsn, "gemm_ms": ms_gemm,
                          "polish_ms": sum(i.ms_polish for i in infos),

@@ -1313,7 +1313,8 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
   // would hold only the longest pairs), and up to 32 pairs per SM: with
   // fewer, the last pairs' latency decides and favours the wider teams over
   // the form with the higher throughput.  Each variant runs twice and its
-  // faster run counts.
+  // faster run counts (once when the sample holds 1024 pairs or more: such a
+  // run is long enough to time to about 1%).
   int& nt = S.tuned_nt[fp32 ? 1 : 0];
   if (S.forced >= BV_TEAM_SPLIT && !fp32) {
     set_err(c, "fram_solve_batched: the team kernel runs the mixed precisions only");
@@ -1344,7 +1345,7 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
       cands.push_back(BV_TEAM64);
     }
     for (int cand : cands) {
-      for (int rep = 0; rep < 2; ++rep) {
+      for (int rep = 0; rep < (m >= 1024 ? 1 : 2); ++rep) {
         BT_CUDA(cudaMemsetAsync(S.queue, 0, 4, s), "memset");
         BT_CUDA(cudaEventRecord(c->ev0, s), "event");
         if (launch_batched_variant(fp32, t, cand, c->num_sms, s) < 0)

@@ -10,8 +10,8 @@ import bench
 
 def test_sdsn_traffic_measured_and_scaled():
     # n = 1000: the ncu figure, independent of the sweep count (on chip).
-    assert bench.sdsn_traffic(1000, 4, 196.0) == 4.16e6
-    assert bench.sdsn_traffic(1000, 4, 10.0) == 4.16e6
+    assert bench.sdsn_traffic(1000, 4, 196.0) == 4.17e6
+    assert bench.sdsn_traffic(1000, 4, 10.0) == 4.17e6
     # n >= 6144: bytes per element and pass times n^2 (sweeps + 1); at the
     # captured size and sweep count it gives back the capture (59.16 GB).
     t = bench.sdsn_traffic(6144, 4, 200.0)
@@ -38,3 +38,22 @@ def test_batch_roofline_counts_algorithmic_flops():
 def test_job_rate_is_units_of_all_ranks_over_the_slowest():
     assert bench.job_rate(10, 1, 2.0) == pytest.approx(5.0)
     assert bench.job_rate(10, 4, 2.0) == pytest.approx(20.0)
+
+
+def test_cluster_sdsn_roofline_is_alu_on_the_cluster_sms():
+    # n = 1000 FP32: the whole iterate stays in one 16-CTA cluster, so the
+    # roofline counts 5 n^2 FP32 operations per sweep against 16 SMs x 128
+    # lanes x 2.07 GHz, with the whole-GPU fraction beside it.
+    info = SimpleNamespace(ms_sdsn=6.7, ms_gemm=0.35, ms_polish=1.06, ms_update=0.33,
+                           ms_rounding=0.18, ms_total=8.9, total_sweeps=2040, polish_sweeps=40,
+                           outer_iters=10)
+    r = bench.roofline([info], 1000, "tf32", {"hbm_gbs": 6800.0}, "measured")
+    assert r["bound"] == "alu" and r["kernel"] == "sdsn_cluster_kernel<2, 8>"
+    assert r["peak"] == pytest.approx(16 * 128 * 2.07 / 1e3)
+    assert r["achieved"] == pytest.approx(5e6 * 2000 / 6.7e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["gpu_frac"] == pytest.approx(r["achieved"] / (152 * 128 * 2.07 / 1e3))
+    assert r["traffic"] == 4.17e6
+    # above the cluster range the FP32 SDSN streams through HBM
+    big = SimpleNamespace(**{**vars(info), "ms_sdsn": 490.0})
+    assert bench.roofline([big], 8192, "tf32", {"hbm_gbs": 6800.0}, "measured")["bound"] == "hbm"
