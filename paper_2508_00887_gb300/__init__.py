@@ -128,6 +128,16 @@ def exported_symbols():
 
 
 # ---------------------------------------------------------------- marshalling
+_DTYPE_NAMES = {}  # torch dtype object -> "float64", ... (str() of a dtype is slow)
+
+
+def _dtype_name(dt):
+    name = _DTYPE_NAMES.get(dt)
+    if name is None:
+        name = _DTYPE_NAMES[dt] = str(dt).split(".")[-1]
+    return name
+
+
 def _addr(x, dtype="float64"):
     """Address of a contiguous buffer (torch tensor, numpy array or int)."""
     if x is None:
@@ -137,7 +147,7 @@ def _addr(x, dtype="float64"):
     if hasattr(x, "data_ptr"):            # torch.Tensor
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
-        if str(x.dtype).split(".")[-1] != dtype:
+        if _dtype_name(x.dtype) != dtype:
             raise ValueError(f"tensor dtype must be {dtype}, got {x.dtype}")
         return x.data_ptr()
     if hasattr(x, "ctypes"):              # numpy.ndarray
@@ -147,6 +157,46 @@ def _addr(x, dtype="float64"):
             raise ValueError(f"array dtype must be {dtype}, got {x.dtype}")
         return x.ctypes.data
     raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _addrs(xs, dtype="float64"):
+    """_addr over a list; lists of torch tensors or numpy arrays take a fast
+    path (the dtype is checked once per distinct dtype object, by identity)."""
+    if not xs:
+        return []
+    if not hasattr(xs[0], "data_ptr"):
+        if not hasattr(xs[0], "ctypes"):
+            return [_addr(x, dtype) for x in xs]
+        out = []
+        seen = None
+        for x in xs:
+            if x is None or not hasattr(x, "ctypes"):
+                out.append(_addr(x, dtype))
+                continue
+            dt = x.dtype
+            if dt is not seen:
+                if dt.name != dtype:
+                    raise ValueError(f"array dtype must be {dtype}, got {dt}")
+                seen = dt
+            if not x.flags.c_contiguous:
+                raise ValueError("array must be C-contiguous")
+            out.append(x.ctypes.data)
+        return out
+    out = []
+    seen = None
+    for x in xs:
+        if x is None or not hasattr(x, "data_ptr"):
+            out.append(_addr(x, dtype))
+            continue
+        dt = x.dtype
+        if dt is not seen:
+            if _dtype_name(dt) != dtype:
+                raise ValueError(f"tensor dtype must be {dtype}, got {dt}")
+            seen = dt
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        out.append(x.data_ptr())
+    return out
 
 
 def _check(ctx, status):
@@ -214,17 +264,19 @@ def fram_solve(ctx, n, A, B, K=None, params=None, X_out=None, perm_out=None, che
 def fram_solve_batched(ctx, ns, As, Bs, params=None, X_outs=None, perm_outs=None, check=True):
     count = len(ns)
     n_arr = (C.c_int * count)(*ns)
-    a_arr = (_P * count)(*[_addr(a) for a in As])
-    b_arr = (_P * count)(*[_addr(b) for b in Bs])
-    x_arr = (_P * count)(*[_addr(x) for x in X_outs]) if X_outs is not None else None
-    p_arr = (_P * count)(*[_addr(p, "int32") for p in perm_outs])
+    a_arr = (_P * count)(*_addrs(As))
+    b_arr = (_P * count)(*_addrs(Bs))
+    x_arr = (_P * count)(*_addrs(X_outs)) if X_outs is not None else None
+    p_arr = (_P * count)(*_addrs(perm_outs, "int32"))
     infos = (FramInfo * max(count, 1))()
     st = load().fram_solve_batched(ctx, count, n_arr, a_arr, b_arr,
                                    C.byref(params) if params is not None else None,
                                    x_arr, p_arr, infos)
     if check:
         _check(ctx, st)
-    return st, list(infos)[:count]
+    # The ctypes array itself (indexable, iterable, len() == count): copying
+    # thousands of structs into a list would cost more than the call.
+    return st, (infos if count > 0 else [])
 
 
 def fram_set_batched_kernel(ctx, variant, check=True):

@@ -2,6 +2,7 @@
 // the host side of Alg. 1 (arXiv 2508.00887).  Every arithmetic step runs in
 // this library's kernels; the host only sequences launches and reads back a
 // few scalars per outer iteration (delta and the SDSN status).
+#include <cuda.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -54,6 +55,39 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+using RangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+RangeFn range_fn() {
+  static const RangeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<RangeFn>(p);
+    cudaGetLastError();
+    return static_cast<RangeFn>(nullptr);
+  }();
+  return fn;
+}
+}  // namespace
+
+bool PtrClassifier::is_device(const void* p) {
+  if (p == nullptr) return false;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  auto it = std::upper_bound(ranges_.begin(), ranges_.end(), std::make_pair(a, UINTPTR_MAX));
+  if (it != ranges_.begin() && a < std::prev(it)->second) return true;
+  if (!is_device_ptr(p)) return false;
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  const RangeFn fn = range_fn();
+  if (fn && fn(&base, &size, (CUdeviceptr)a) == CUDA_SUCCESS && size > 0) {
+    const std::pair<uintptr_t, uintptr_t> r((uintptr_t)base, (uintptr_t)base + size);
+    ranges_.insert(std::upper_bound(ranges_.begin(), ranges_.end(), r), r);
+  }
+  return true;
 }
 
 int round_ld(int n) { return ((n + 127) / 128) * 128; }

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "fram_ctx.h"
@@ -775,51 +776,56 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
   int t = 0, sweeps_total = 0;
   while (t < a.max_outer) {
     // Step 5, T = A N: column c of T from column c of N and rows of A^T.
+    // Column c of N goes to row c of the (A N)^T region first, which only
+    // this lane reads and then overwrites with column c of T: the k loop can
+    // then index it at run time (a register array cannot be), which keeps
+    // the loop rolled and the kernel's code small.
+    team_sync<TE>(bar_id);  // the previous iteration's reads of (A N)^T are done
+    float4* const own = reinterpret_cast<float4*>(TsT + c * SA);  // (A N)^T[c][i] = T[i][c]
+#pragma unroll
+    for (int q = 0; q < TE / 4; ++q)
+      own[q] = make_float4(ncol[4 * q], ncol[4 * q + 1], ncol[4 * q + 2], ncol[4 * q + 3]);
 #pragma unroll
     for (int i = 0; i < TE; ++i) y[i] = 0.f;
+#pragma unroll 1
+    for (int k4 = 0; k4 < n; k4 += 4) {
+      const float4 n4 = own[k4 >> 2];
+      const float nk4[4] = {n4.x, n4.y, n4.z, n4.w};
 #pragma unroll
-    for (int k = 0; k < TE; ++k) {
-      // One k at a time: without the barrier the unrolled loop hoists the
-      // loads of many rows at once and runs out of registers.
-      asm volatile("" ::: "memory");
-      if (k < n) {
-        const float nk = ncol[k];
-        const float4* ar = reinterpret_cast<const float4*>(AsT + k * SA);
+      for (int h = 0; h < 4; ++h) {
+        const int k = k4 + h;
+        if (k < n) {
+          const float nk = nk4[h];
+          const float4* ar = reinterpret_cast<const float4*>(AsT + k * SA);
 #pragma unroll
-        for (int q = 0; q < TE / 4; ++q) {
-          const float4 av = ar[q];
-          y[4 * q] = fmaf(av.x, nk, y[4 * q]);
-          y[4 * q + 1] = fmaf(av.y, nk, y[4 * q + 1]);
-          y[4 * q + 2] = fmaf(av.z, nk, y[4 * q + 2]);
-          y[4 * q + 3] = fmaf(av.w, nk, y[4 * q + 3]);
+          for (int q = 0; q < TE / 4; ++q) {
+            const float4 av = ar[q];
+            y[4 * q] = fmaf(av.x, nk, y[4 * q]);
+            y[4 * q + 1] = fmaf(av.y, nk, y[4 * q + 1]);
+            y[4 * q + 2] = fmaf(av.z, nk, y[4 * q + 2]);
+            y[4 * q + 3] = fmaf(av.w, nk, y[4 * q + 3]);
+          }
         }
       }
     }
-    team_sync<TE>(bar_id);  // the previous iteration's reads of (A N)^T are done
-    {
-      float4* tr = reinterpret_cast<float4*>(TsT + c * SA);  // (A N)^T[c][i] = T[i][c]
 #pragma unroll
-      for (int q = 0; q < TE / 4; ++q)
-        tr[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-    }
+    for (int q = 0; q < TE / 4; ++q)
+      own[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
     team_sync<TE>(bar_id);
     // X = T B: column c of X from column c of B and rows of T^T.
 #pragma unroll
     for (int i = 0; i < TE; ++i) y[i] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+      const float bk = Bs[k * SB + c];
+      const float4* tr = reinterpret_cast<const float4*>(TsT + k * SA);
 #pragma unroll
-    for (int k = 0; k < TE; ++k) {
-      asm volatile("" ::: "memory");
-      if (k < n) {
-        const float bk = Bs[k * SB + c];
-        const float4* tr = reinterpret_cast<const float4*>(TsT + k * SA);
-#pragma unroll
-        for (int q = 0; q < TE / 4; ++q) {
-          const float4 tv = tr[q];
-          y[4 * q] = fmaf(tv.x, bk, y[4 * q]);
-          y[4 * q + 1] = fmaf(tv.y, bk, y[4 * q + 1]);
-          y[4 * q + 2] = fmaf(tv.z, bk, y[4 * q + 2]);
-          y[4 * q + 3] = fmaf(tv.w, bk, y[4 * q + 3]);
-        }
+      for (int q = 0; q < TE / 4; ++q) {
+        const float4 tv = tr[q];
+        y[4 * q] = fmaf(tv.x, bk, y[4 * q]);
+        y[4 * q + 1] = fmaf(tv.y, bk, y[4 * q + 1]);
+        y[4 * q + 2] = fmaf(tv.z, bk, y[4 * q + 2]);
+        y[4 * q + 3] = fmaf(tv.w, bk, y[4 * q + 3]);
       }
     }
     float lm = -INFINITY;
@@ -1200,15 +1206,18 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
   std::vector<BatchDesc> desc(count);
   size_t mat = 0, vec = 0;
   int in_dev = 0, out_dev = 0;
+  PtrClassifier pc;  // thousands of pointers, few allocations
   for (int k = 0; k < count; ++k) {
     const int i = order[k];
     desc[k] = BatchDesc{n[i], i, (long long)mat, (long long)vec};
     mat += (size_t)n[i] * n[i];
     vec += (size_t)n[i];
-    in_dev += (is_device_ptr(A[i]) ? 1 : 0) + (is_device_ptr(B[i]) ? 1 : 0);
-    const bool xd = !wantX || X_out[i] == nullptr || is_device_ptr(X_out[i]);
-    const bool xh = !wantX || X_out[i] == nullptr || !is_device_ptr(X_out[i]);
-    const bool pd = is_device_ptr(perm_out[i]);
+    in_dev += (pc.is_device(A[i]) ? 1 : 0) + (pc.is_device(B[i]) ? 1 : 0);
+    const bool xnone = !wantX || X_out[i] == nullptr;
+    const bool xdev = !xnone && pc.is_device(X_out[i]);
+    const bool xd = xnone || xdev;
+    const bool xh = xnone || !xdev;
+    const bool pd = pc.is_device(perm_out[i]);
     out_dev += (pd && xd) ? 1 : ((!pd && xh) ? 0 : -count - 1);
   }
   if (in_dev != 0 && in_dev != 2 * count) {
@@ -1277,10 +1286,38 @@ fram_status solve_small_batch(fram_ctx* c, const std::vector<int>& idx, const in
     if (cudaPeekAtLastError() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "gather");
     c->launches += 1;
   } else {
-    for (int k = 0; k < count; ++k) {
-      const BatchDesc& d = desc[k];
-      memcpy(S.hA + d.off_mat, A[d.index], (size_t)d.n * d.n * 8);
-      memcpy(S.hB + d.off_mat, B[d.index], (size_t)d.n * d.n * 8);
+    // Pack the host inputs into the pinned staging arena: a memory-bound
+    // loop, split over up to 8 threads by byte offset for large batches.
+    auto pack = [&](int k0, int k1) {
+      for (int k = k0; k < k1; ++k) {
+        const BatchDesc& d = desc[k];
+        memcpy(S.hA + d.off_mat, A[d.index], (size_t)d.n * d.n * 8);
+        memcpy(S.hB + d.off_mat, B[d.index], (size_t)d.n * d.n * 8);
+      }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = mat * 16 >= (16u << 20) ? (int)std::min(8u, hw > 1 ? hw : 1u) : 1;
+    if (nth <= 1) {
+      pack(0, count);
+    } else {
+      std::vector<std::thread> th;
+      int k0 = 0;
+      for (int t = 1; t <= nth && k0 < count; ++t) {
+        const size_t until = mat * (size_t)t / (size_t)nth;  // cumulative element bound
+        int k1 = k0;
+        while (k1 < count && (t == nth || (size_t)desc[k1].off_mat < until)) ++k1;
+        if (k1 > k0) {
+          try {
+            th.emplace_back(pack, k0, k1);
+          } catch (...) {  // no thread to be had: this one packs the rest
+            pack(k0, count);
+            k0 = count;
+            break;
+          }
+        }
+        k0 = k1;
+      }
+      for (auto& x : th) x.join();
     }
     BT_CUDA(cudaMemcpyAsync(S.A, S.hA, mat * 8, cudaMemcpyHostToDevice, s), "copy inputs");
     BT_CUDA(cudaMemcpyAsync(S.B, S.hB, mat * 8, cudaMemcpyHostToDevice, s), "copy inputs");

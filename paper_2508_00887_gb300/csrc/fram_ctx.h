@@ -3,9 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/fram.h"
 #include "fram_internal.cuh"
@@ -81,6 +85,17 @@ namespace fram {
 void set_err(fram_ctx* c, const char* fmt, ...);
 fram_status cuda_fail(fram_ctx* c, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
+// is_device_ptr for many pointers in one call: remembers the address range
+// of every device allocation it has classified (cuMemGetAddressRange), so a
+// pointer inside a known range needs no driver query.  Valid while those
+// allocations stay alive, i.e. within one API call.
+class PtrClassifier {
+ public:
+  bool is_device(const void* p);
+
+ private:
+  std::vector<std::pair<uintptr_t, uintptr_t>> ranges_;  // [base, end), sorted by base
+};
 int round_ld(int n);
 fram_status ensure_workspace(fram_ctx* c, int n);
 fram_status ensure_mixed(fram_ctx* c, int n);
