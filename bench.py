@@ -789,7 +789,7 @@ def roofline(infos, n, precision, pk, src):
             "peak": pk.get("hbm_gbs"), "unit": "GB/s",
             "per_launch_us": 1e3 * ms_sdsn / max(launches, 1),
             "per_sweep_us": 1e3 * ms_sdsn / max(sweeps, 1)}
-    if s == 4 and 96 < n <= 1024:
+    if s == 4 and 2 <= n <= 1024:
         # The FP32 iterate stays on chip in one thread-block cluster (DRAM
         # carries X once), so the sweep is bound by its arithmetic and
         # exchange on the cluster's SMs, not by HBM: 5 n^2 FP32 operations

@@ -272,7 +272,7 @@ int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned lo
                double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
                SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
-// FP32 SDSN of one problem in one thread-block cluster (96 < n <= 1024, mode
+// FP32 SDSN of one problem in one thread-block cluster (2 <= n <= 1024, mode
 // 0, no gate): 1 launched, 0 not applicable (use the grid form), -1 error.
 int launch_sdsn_cluster(const SdsnLaunch& L, cudaStream_t s);
 // Cluster class of a problem (0: the cluster form does not apply); problems

@@ -781,7 +781,7 @@ int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
 int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   if (!L.in_fp32 && !L.out_fp32) return launch_sdsn_t<double, double>(L, num_sms, s);
   if (L.in_fp32 && L.out_fp32) {
-    // 96 < n <= 1024: the whole FP32 iterate in one cluster (no grid barrier).
+    // 2 <= n <= 1024: the whole FP32 iterate in one cluster (no grid barrier).
     const int k = launch_sdsn_cluster(L, s);
     if (k != 0) return k;
     return launch_sdsn_t<float, float>(L, num_sms, s);

@@ -1,4 +1,4 @@
-// SDSN (Alg. 2 of arXiv 2508.00887) in FP32 for 96 < n <= 1024, held
+// SDSN (Alg. 2 of arXiv 2508.00887) in FP32 for 2 <= n <= 1024, held
 // entirely on chip by ONE thread-block cluster of s x s CTAs (s = 1, 2 or 4;
 // 16 CTAs is a non-portable cluster size).
 //
@@ -544,7 +544,7 @@ int cluster_side(int n) { return n <= 256 ? 1 : n <= 512 ? 2 : 4; }
 // Fill the problem descriptor; false when this form does not apply.
 bool make_cluster_problem(const SdsnLaunch& L, ClusterK& k) {
   if (!L.in_fp32 || !L.out_fp32 || L.mode != 0 || L.gate != nullptr) return false;
-  if (L.n <= 96 || L.n > 1024) return false;
+  if (L.n < 2 || L.n > 1024) return false;
   k = ClusterK{};
   k.n = L.n;
   k.s = cluster_side(L.n);

@@ -395,7 +395,7 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       }
     };
     waves(L64);
-    // FP32 problems of 96 < n <= 1024 run on one cluster each, as fram_solve
+    // FP32 problems of 2 <= n <= 1024 run on one cluster each, as fram_solve
     // runs them: one launch per cluster class, any number of problems.
     {
       std::vector<SdsnLaunch> grid32, cls[7];

@@ -11,8 +11,8 @@ Covered variants (the grid and tile follow from n alone):
     iterate resident in L2 (six groups per lane);
   * n = 8192, stride 8192: the dense workload's size, 256 MB iterate
     streamed from HBM every sweep (six groups per lane);
-  * small and ragged sizes: one CTA (n <= 96), odd n and unaligned strides
-    (the scalar, non-vector path).
+  * small and ragged sizes: the one-CTA cluster form (n <= 256), odd n and
+    unaligned strides.
 
 Tolerance, derived from the arithmetic.  The oracle runs the same sweeps in
 FP64 on the same (FP32-representable) input.  P1 (an affine projection) and
