@@ -586,7 +586,7 @@ fram_status fram_create(fram_ctx** out, int device, size_t budget, void* stream)
   for (int i = 0; i < 5 && ev_ok; ++i) ev_ok = cudaEventCreate(&c->evp[i]) == cudaSuccess;
   if (!ev_ok) {
     cudaGetLastError();
-    delete c;
+    fram_destroy(c);  // releases the events and stream made so far
     return FRAM_ERR_CUDA;
   }
   *out = c;

@@ -59,8 +59,6 @@ struct ClusterK {
   SdsnStats* stats;
 };
 
-__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~size_t(15); }
-
 // Shared-memory layout (floats unless noted), fixed for a kernel variant.
 // Tiles are padded to TCP = 128 G columns and kMaxTile rows: every lane owns
 // G whole 16-byte groups and every warp 16 rows, so the sweep loop has no
@@ -157,12 +155,6 @@ __device__ __forceinline__ uint32_t remote(const void* local, uint32_t rank) {
 __device__ __forceinline__ float ld_remote_f32(uint32_t addr) {
   float v;
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ double ld_remote_f64(uint32_t addr) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
   return v;
 }
 
