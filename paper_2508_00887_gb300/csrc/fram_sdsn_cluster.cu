@@ -399,16 +399,20 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
   // columns, each summed over the s CTAs in a fixed order.
   auto gather = [&](const int par, const int k) {
     if (warp == 0) {
-      // S: the s*s tile totals summed in a fixed order as a double-float
-      // (TwoSum: exact up to the final hi + lo rounding, ~2^-48 relative).
-      float t = 0.f;
-      if (lane < s * s) t = s > 1 ? ld_remote_f32(remote(&tpub[par], (uint32_t)lane)) : tpub[par];
+      // S: the s*s tile totals summed as a double-float by a pairwise tree
+      // over lanes in a fixed order (TwoSum at every node: exact up to the
+      // rounding of the low parts, ~2^-48 relative).  A tree, not a chain:
+      // the other warps wait for S at the next barrier.
       float hi = 0.f, lo = 0.f;
-      for (int q = 0; q < s * s; ++q) {
-        const float tq = __shfl_sync(0xffffffffu, t, q);
+      if (lane < s * s) hi = s > 1 ? ld_remote_f32(remote(&tpub[par], (uint32_t)lane)) : tpub[par];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        if (o >= s * s) continue;  // uniform: s*s is 1, 4 or 16
+        const float ohi = __shfl_down_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_down_sync(0xffffffffu, lo, o);
         float e;
-        two_sum(hi, tq, hi, e);
-        lo += e;
+        two_sum(hi, ohi, hi, e);
+        lo = (lo + olo) + e;
       }
       {
         float e;
