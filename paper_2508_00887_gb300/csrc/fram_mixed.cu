@@ -73,6 +73,11 @@ __global__ void transpose_lp_kernel(const double* __restrict__ src, void* __rest
 // Alg. 1 steps 7-8 in FP64 on the n x n block, plus the transposed
 // low-precision copy of the new N for the next gradient.  Deterministic
 // delta: fixed tile ownership, fixed reduction trees, last-block combine.
+// The update is written N + alpha (D - N), the same value as (1 - alpha) N +
+// alpha D in exact arithmetic, and N_new - N = alpha (D - N), so that
+// ||N_new - N||^2 = alpha^2 sum (D - N)^2: per element one subtraction and
+// three FMAs instead of six FP64 operations (GB300's FP64 pipe bounds this
+// kernel).
 template <int KIND>
 __device__ __forceinline__ void update_mixed_body(double* __restrict__ N,
                                                   const double* __restrict__ D, int ld, int n,
@@ -82,7 +87,6 @@ __device__ __forceinline__ void update_mixed_body(double* __restrict__ N,
   __shared__ double tile[kT][kT + 1];
   __shared__ double red[2][8];
   __shared__ int s_last;
-  const double beta = 1.0 - alpha;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int tiles = (n + kT - 1) / kT;
   double d2 = 0.0, n2 = 0.0;
@@ -94,10 +98,10 @@ __device__ __forceinline__ void update_mixed_body(double* __restrict__ N,
       if (i < n && j < n) {
         const size_t e = (size_t)i * ld + j;
         const double old = N[e];
-        nn = __dadd_rn(__dmul_rn(beta, old), __dmul_rn(alpha, D[e]));
-        const double d = __dsub_rn(nn, old);
+        const double t = __dsub_rn(D[e], old);
+        nn = __fma_rn(alpha, t, old);
         N[e] = nn;
-        d2 = fma(d, d, d2);
+        d2 = fma(t, t, d2);
         n2 = fma(nn, nn, n2);
       }
       tile[r][tx] = nn;
@@ -131,18 +135,32 @@ __device__ __forceinline__ void update_mixed_body(double* __restrict__ N,
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (warp == 0) {
+  {
+    // All 256 threads of the last block read the partials (fixed stride,
+    // fixed tree): one round of L2 latency instead of nblk / 32 in a row.
+    const int tid = ty * 32 + tx;
     double a = 0.0, b = 0.0;
-    for (int k = lane; k < nblk; k += 32) {
+#pragma unroll 4
+    for (int k = tid; k < nblk; k += 256) {
       a += __ldcg(&partials[2 * k]);
       b += __ldcg(&partials[2 * k + 1]);
     }
     a = warp_sum(a);
     b = warp_sum(b);
     if (lane == 0) {
-      st->sum_d2 = a;
+      red[0][warp] = a;
+      red[1][warp] = b;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double a = lane < 8 ? red[0][lane] : 0.0, b = lane < 8 ? red[1][lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      st->sum_d2 = alpha * alpha * a;
       st->sum_n2 = b;
-      st->delta = sqrt(a) / sqrt(b);
+      st->delta = alpha * sqrt(a) / sqrt(b);
       *ticket = 0u;
     }
   }
