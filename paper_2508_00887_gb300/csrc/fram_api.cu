@@ -310,10 +310,13 @@ fram_status validate_and_scale(fram_ctx* c, int n, const double* A0, const doubl
     set_err(c, "all inputs are zero: SDSN step 1 is undefined");
     return FRAM_ERR_DEGENERATE;
   }
-  const double s = sqrt(cc);
-  FR_LAUNCH(launch_scale(A0, n, s, true, w.As, ld, c->stream), "scale kernel");
-  FR_LAUNCH(launch_scale(B0, n, s, true, w.Bs, ld, c->stream), "scale kernel");
-  if (K0) FR_LAUNCH(launch_scale(K0, n, cc, true, w.Ks, ld, c->stream), "scale kernel");
+  // A / sqrt(c) and B / sqrt(c) as one multiply by the reciprocal (an FP64
+  // division per element is a long sequence on GB300's FP64 pipe); the
+  // batched and served paths scale the same way.
+  const double inv_s = 1.0 / sqrt(cc);
+  FR_LAUNCH(launch_scale(A0, n, inv_s, w.As, ld, c->stream), "scale kernel");
+  FR_LAUNCH(launch_scale(B0, n, inv_s, w.Bs, ld, c->stream), "scale kernel");
+  if (K0) FR_LAUNCH(launch_scale(K0, n, 1.0 / cc, w.Ks, ld, c->stream), "scale kernel");
   *scale_c = cc;
   return FRAM_OK;
 }
@@ -723,10 +726,10 @@ fram_status fram_gradient(fram_ctx* c, int n, const double* A, const double* Nm,
   FR_TRY(ensure_workspace(c, n));
   Workspace& w = c->ws;
   const int ld = round_ld(n);
-  FR_LAUNCH(launch_scale(A, n, 1.0, false, w.As, ld, c->stream), "copy");
-  FR_LAUNCH(launch_scale(B, n, 1.0, false, w.Bs, ld, c->stream), "copy");
-  FR_LAUNCH(launch_scale(Nm, n, 1.0, false, w.N, ld, c->stream), "copy");
-  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, false, w.Ks, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(A, n, 1.0, w.As, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(B, n, 1.0, w.Bs, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(Nm, n, 1.0, w.N, ld, c->stream), "copy");
+  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, w.Ks, ld, c->stream), "copy");
   FR_TRY(prepare_sparse(c, n));
   FR_TRY(fp64_gradient(c, n, K != nullptr, lambda, nullptr));
   FR_CUDA(cudaMemcpy2DAsync(X, (size_t)n * sizeof(double), w.X, (size_t)ld * sizeof(double),
@@ -753,10 +756,10 @@ fram_status fram_gradient_lowp(fram_ctx* c, int n, const double* A, const double
   FR_TRY(ensure_mixed(c, n));
   Workspace& w = c->ws;
   const int ld = round_ld(n);
-  FR_LAUNCH(launch_scale(A, n, 1.0, false, w.As, ld, c->stream), "copy");
-  FR_LAUNCH(launch_scale(B, n, 1.0, false, w.Bs, ld, c->stream), "copy");
-  FR_LAUNCH(launch_scale(Nm, n, 1.0, false, w.N, ld, c->stream), "copy");
-  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, false, w.Ks, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(A, n, 1.0, w.As, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(B, n, 1.0, w.Bs, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(Nm, n, 1.0, w.N, ld, c->stream), "copy");
+  if (K) FR_LAUNCH(launch_scale(K, n, 1.0, w.Ks, ld, c->stream), "copy");
   float* X32 = nullptr;
   FR_TRY(mixed_gradient(c, n, K != nullptr, lambda, precision == FRAM_PREC_MIXED_BF16 ? 0 : 1,
                         &X32));
@@ -881,7 +884,7 @@ fram_status fram_fra_exact(fram_ctx* c, int n, const double* X, double* D, doubl
   FR_TRY(ensure_workspace(c, n));
   Workspace& w = c->ws;
   const int ld = round_ld(n);
-  FR_LAUNCH(launch_scale(X, n, 1.0, false, w.X, ld, c->stream), "copy");
+  FR_LAUNCH(launch_scale(X, n, 1.0, w.X, ld, c->stream), "copy");
   FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream), "memset");
   FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
   FR_LAUNCH(launch_max(w.X, ld, n, &w.scal->xmax_key, c->stream), "max kernel");

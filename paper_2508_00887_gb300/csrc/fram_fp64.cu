@@ -48,53 +48,114 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- validate
-// One block per row (grid-strided): finite and >= 0 checks, max, and the
-// largest asymmetry |M_ij - M_ji| for A and B.
+// Finite and >= 0 checks, the max, and the largest asymmetry |M_ij - M_ji|
+// (A and B).  One 32 x 32 tile pair per step: tile (bi, bj), bi <= bj, and
+// its mirror (bj, bi), both read coalesced into shared memory, so the
+// transposed element is a shared-memory read.  The checks and the maxima run
+// on bit patterns (integer instructions; nonnegative doubles order like their
+// bits); only the asymmetry takes an FP64 subtraction.
+constexpr int kVT = 32;
+
+__device__ __forceinline__ void check_entry(double a, int& bad, unsigned long long& mx) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(a);
+  const bool nonfinite = ((u >> 52) & 0x7FFull) == 0x7FFull;
+  const bool negative = (u >> 63) != 0ull && (u << 1) != 0ull;  // -0.0 counts as 0
+  if (nonfinite || negative) {
+    bad = 1;
+    return;
+  }
+  if ((u << 1) == 0ull) u = 0ull;
+  mx = u > mx ? u : mx;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v,
+                                                            unsigned long long* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  unsigned long long r = 0ull;
+  if (warp == 0) {
+    r = lane < kRowThreads / 32 ? red[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, r, o);
+      r = w > r ? w : r;
+    }
+  }
+  return r;  // valid in thread 0
+}
+
 __global__ void __launch_bounds__(kRowThreads) validate_kernel(const double* __restrict__ A,
                                                                const double* __restrict__ B,
                                                                const double* __restrict__ K, int n,
                                                                ValidateStats* st) {
-  __shared__ double red[kRowThreads / 32];
+  __shared__ double t0[kVT][kVT + 1], t1[kVT][kVT + 1];
+  __shared__ unsigned long long red[kRowThreads / 32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int T = (n + kVT - 1) / kVT;
   const double* mats[3] = {A, B, K};
   for (int which = 0; which < 3; ++which) {
     const double* M = mats[which];
     if (M == nullptr) continue;
-    double mx = 0.0, asym = 0.0;
+    unsigned long long mx = 0ull, as = 0ull;
     int bad = 0;
-    for (int i = blockIdx.x; i < n; i += gridDim.x) {
-      for (int j = threadIdx.x; j < n; j += kRowThreads) {
-        const double a = M[(size_t)i * n + j];
-        if (!isfinite(a) || a < 0.0) {
-          bad = 1;
-          continue;
+    for (int p = blockIdx.x; p < T * T; p += gridDim.x) {
+      const int bi = p / T, bj = p % T;
+      if (bi > bj) continue;  // the same for the whole block
+      __syncthreads();        // the previous pair's reads are done
+      for (int r = ty; r < kVT; r += kRowThreads / 32) {
+        const int i = bi * kVT + r, j = bj * kVT + tx;
+        t0[r][tx] = (i < n && j < n) ? M[(size_t)i * n + j] : 0.0;
+        const int i2 = bj * kVT + r, j2 = bi * kVT + tx;
+        t1[r][tx] = (i2 < n && j2 < n) ? M[(size_t)i2 * n + j2] : 0.0;
+      }
+      __syncthreads();
+      for (int r = ty; r < kVT; r += kRowThreads / 32) {
+        const int i = bi * kVT + r, j = bj * kVT + tx;
+        if (i < n && j < n) {
+          const double a = t0[r][tx];
+          check_entry(a, bad, mx);
+          if (which < 2) {
+            const double t = t1[tx][r];  // M[j][i]
+            const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+            const unsigned long long ut = (unsigned long long)__double_as_longlong(t);
+            if (((ua >> 52) & 0x7FFull) != 0x7FFull && ((ut >> 52) & 0x7FFull) != 0x7FFull) {
+              const unsigned long long d =
+                  (unsigned long long)__double_as_longlong(a - t) & 0x7FFFFFFFFFFFFFFFull;
+              as = d > as ? d : as;
+            }
+          }
         }
-        mx = fmax(mx, a);
-        if (which < 2) {
-          const double t = M[(size_t)j * n + i];
-          if (isfinite(t)) asym = fmax(asym, fabs(a - t));
-        }
+        const int i2 = bj * kVT + r, j2 = bi * kVT + tx;
+        if (bi != bj && i2 < n && j2 < n) check_entry(t1[r][tx], bad, mx);
       }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->bad_value[which], 1);
-    const double bmx = block_max<kRowThreads>(mx, red);
-    if (threadIdx.x == 0) atomic_max_nonneg(&st->maxbits[which], bmx);
+    const unsigned long long bmx = block_max_u64(mx, red);
+    if (threadIdx.x == 0 && bmx) atomicMax(&st->maxbits[which], bmx);
     if (which < 2) {
-      const double bas = block_max<kRowThreads>(asym, red);
-      if (threadIdx.x == 0) atomic_max_nonneg(&st->asymbits[which], bas);
+      const unsigned long long bas = block_max_u64(as, red);
+      if (threadIdx.x == 0 && bas) atomicMax(&st->asymbits[which], bas);
     }
   }
 }
 
 // ---------------------------------------------------------------- scale
-// dst (ld x ld, zero padding) = src (n x n contiguous) / div  or  * mul.
-__global__ void scale_kernel(const double* __restrict__ src, int n, double v, int divide,
+// dst (ld x ld, zero padding) = src (n x n contiguous) * v.
+__global__ void scale_kernel(const double* __restrict__ src, int n, double v,
                              double* __restrict__ dst, int ld) {
   for (int i = blockIdx.x; i < ld; i += gridDim.x) {
     for (int j = threadIdx.x; j < ld; j += blockDim.x) {
       double o = 0.0;
       if (i < n && j < n) {
         const double a = src[(size_t)i * n + j];
-        o = divide ? a / v : a * v;
+        o = a * v;
       }
       dst[(size_t)i * ld + j] = o;
     }
@@ -351,13 +412,13 @@ int grid_rows(int rows) { return rows < 1 ? 1 : (rows < 1184 ? rows : 1184); }
 // ---------------------------------------------------------------- launchers
 int launch_validate(const double* A, const double* B, const double* K, int n, ValidateStats* st,
                     cudaStream_t s) {
-  validate_kernel<<<grid_rows(n), kRowThreads, 0, s>>>(A, B, K, n, st);
+  const int T = (n + kVT - 1) / kVT;
+  validate_kernel<<<grid_rows(T * T), kRowThreads, 0, s>>>(A, B, K, n, st);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_scale(const double* src, int n, double v, bool divide, double* dst, int ld,
-                 cudaStream_t s) {
-  scale_kernel<<<grid_rows(ld), kRowThreads, 0, s>>>(src, n, v, divide ? 1 : 0, dst, ld);
+int launch_scale(const double* src, int n, double v, double* dst, int ld, cudaStream_t s) {
+  scale_kernel<<<grid_rows(ld), kRowThreads, 0, s>>>(src, n, v, dst, ld);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -226,8 +226,8 @@ struct ValidateStats {
 
 int launch_validate(const double* A, const double* B, const double* K, int n,
                     ValidateStats* st, cudaStream_t s);
-int launch_scale(const double* src, int n, double inv, bool divide, double* dst, int ld,
-                 cudaStream_t s);
+// dst (ld x ld, zero padding) = src (n x n contiguous) * v.
+int launch_scale(const double* src, int n, double v, double* dst, int ld, cudaStream_t s);
 int launch_fill_assignment(double* N, int n, int ld, double value, cudaStream_t s);
 int launch_dgemm(const double* A, const double* B, double* C, int ld, int n, const double* K,
                  double lam, unsigned long long* cmax_bits, cudaStream_t s);

@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
   __shared__ int s_k;
   __shared__ double s_h;
   __shared__ int s_aug;
+  __shared__ int s_next;
   const int tid = threadIdx.x;
   unsigned long long *dkey, *tkey;
   double *v, *wmat;
@@ -516,8 +517,23 @@ __global__ void __launch_bounds__(kLapThreads, 1) lap_solve_kernel(const double*
   __syncthreads();
 
   long long total = 0;  // Dijkstra steps of this pass (the same in every thread)
-  for (int f = 0; f < n; ++f) {
-    if (w.rowcol[f] != -1) continue;  // uniform: read after a barrier
+  for (int f = -1;;) {
+    // The next free row after f, kLapThreads rows per step.  A free row is
+    // placed only by its own search, so this takes the free rows in the
+    // order of a row-by-row scan, without a dependent read per row.
+    int nf = n;
+    for (int base = f + 1; base < n; base += kLapThreads) {
+      if (tid == 0) s_next = n;
+      __syncthreads();
+      const int r = base + tid;
+      if (r < n && w.rowcol[r] == -1) atomicMin(&s_next, r);
+      __syncthreads();
+      nf = s_next;
+      __syncthreads();  // every thread has read s_next before it is reset
+      if (nf < n) break;
+    }
+    if (nf >= n) break;
+    f = nf;
     const double* rowf = W + (size_t)f * ldw;
     unsigned long long best = kVisited;
     int bk = 0x7fffffff;  // argmin tie key: j, plus n if column j is assigned

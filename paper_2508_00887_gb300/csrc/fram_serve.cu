@@ -288,9 +288,9 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
           finish(S, r, FRAM_ERR_DEGENERATE, "all inputs are zero");
           continue;
         }
-        const double sq = sqrt(cc);
-        SV_OK(launch_scale(r->A0, r->n, sq, true, r->As, r->ld, s));
-        SV_OK(launch_scale(r->B0, r->n, sq, true, r->Bs, r->ld, s));
+        const double inv_s = 1.0 / sqrt(cc);  // as fram_solve's prescale
+        SV_OK(launch_scale(r->A0, r->n, inv_s, r->As, r->ld, s));
+        SV_OK(launch_scale(r->B0, r->n, inv_s, r->Bs, r->ld, s));
         SV_OK(launch_fill_assignment(r->N, r->n, r->ld, 1.0 / r->n, s));
         if (r->mixed) {
           SV_OK(launch_convert_lp(r->As, r->Alp, r->ld, r->kind, s));
