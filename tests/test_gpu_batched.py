@@ -112,6 +112,21 @@ def test_batched_host_buffers_and_no_x(torch_cuda, ctx):
         assert np.array_equal(a, b) and np.array_equal(c, d) and np.array_equal(c, e)
 
 
+def test_batched_host_buffers_large_batch_packed_in_parallel(torch_cuda, ctx):
+    # The full 4096-pair keypoint batch from host buffers: its 106 MB of
+    # inputs are packed into the staging arena on several threads (batches
+    # of 16 MB and more).  N, the permutations and the per-pair diagnostics
+    # equal those of the same batch from device buffers.
+    pairs = fi.keypoint_batch(4096, seed=5)
+    params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_TF32)
+    Xd, Pd, infd = run_batched(torch_cuda, ctx, pairs, params, device=True)
+    Xh, Ph, infh = run_batched(torch_cuda, ctx, pairs, params, device=False)
+    for a, b, c, d, i, j in zip(Xd, Xh, Pd, Ph, infd, infh):
+        assert np.array_equal(a, b) and np.array_equal(c, d)
+        assert (i.outer_iters, i.total_sweeps, i.objective) == (j.outer_iters, j.total_sweeps,
+                                                                j.objective)
+
+
 def check_batch_equal_accuracy(pairs, P, infos, refs):
     """Equal accuracy of a batch, both ways.  Pairs without outliers (ER
     pairs) must each be within 0.5 pp of accuracy and 1e-3 relative objective
