@@ -590,7 +590,8 @@ struct TeamLayout {
   static constexpr size_t b = a + (size_t)TE * SA * 4;
   static constexpr size_t t = (b + (size_t)TE * SB * 4 + 15) & ~size_t(15);
   static constexpr size_t part = t + (size_t)TE * SA * 4;  // [2][TE] row partials
-  static constexpr size_t red = part + 2 * (size_t)TE * 4;  // 8 doubles
+  static constexpr size_t arow = part + 2 * (size_t)TE * 4;  // [TE] next sweep's a_i
+  static constexpr size_t red = arow + (size_t)TE * 4;       // 8 doubles
   static constexpr size_t u = red + 64;
   static constexpr size_t rowmax = u + (size_t)TE * 8;
   static constexpr size_t rowcol = rowmax + (size_t)TE * 8;
@@ -703,6 +704,7 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
   float* Bs = reinterpret_cast<float*>(region + Lay::b);
   float* TsT = reinterpret_cast<float*>(region + Lay::t);
   float* part = reinterpret_cast<float*>(region + Lay::part);
+  float* arow = reinterpret_cast<float*>(region + Lay::arow);
   double* red = reinterpret_cast<double*>(region + Lay::red);
   double* u = reinterpret_cast<double*>(region + Lay::u);
   double* rowmax = reinterpret_cast<double*>(region + Lay::rowmax);
@@ -847,24 +849,14 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
 #pragma unroll
         for (int i = 0; i < TE; ++i) y[i] *= scale;
       } else {
-        // a_i = 1/n + S/n^2 - r_i/n for all rows, from the row sums.
+        // a_i = 1/n + S/n^2 - r_i/n, formed once per row by the lane that
+        // owns the row (-inf on padding rows, which stay 0).
 #pragma unroll
         for (int q = 0; q < TE / 4; ++q) {
-          const float4 r0 = reinterpret_cast<const float4*>(part)[q];
-          float4 r;
-          if (TE == 64) {
-            const float4 r1 = reinterpret_cast<const float4*>(part + TE)[q];
-            r = make_float4(r0.x + r1.x, r0.y + r1.y, r0.z + r1.z, r0.w + r1.w);
-          } else {
-            r = r0;
-          }
-          const float rr[4] = {r.x, r.y, r.z, r.w};
+          const float4 a4 = reinterpret_cast<const float4*>(arow)[q];
+          const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const int i = 4 * q + h;
-            const float ai = i < n ? cS1 - rr[h] * inv_n_f : -INFINITY;  // padding rows stay 0
-            y[i] = fmaxf((y[i] + ai) - bc, 0.f);
-          }
+          for (int h = 0; h < 4; ++h) y[4 * q + h] = fmaxf((y[4 * q + h] + aa[h]) - bc, 0.f);
         }
       }
       ++k;
@@ -876,7 +868,7 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
       // of row 32 + l): every row by exactly one lane.
       const float v0 = team_rows32<0>(y, lane);
       const float v1 = TE == 64 ? team_rows32<TE == 64 ? 32 : 0>(y, lane) : 0.f;
-      team_sync<TE>(bar_id);  // every lane has read the previous row sums
+      team_sync<TE>(bar_id);  // every lane has read the previous a_i and row sums
       part[wt * TE + lane] = v0;
       if (TE == 64) part[wt * TE + 32 + lane] = v1;
       team_sync<TE>(bar_id);
@@ -892,6 +884,14 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
       Slo = slo;
       bc = c < n ? cs * inv_n_f : INFINITY;  // padding column: stays 0
       cS1 = inv_n_f + (shi * inv_n2_f + slo * inv_n2_f);
+      {
+        // Row 32 wt + lane of the tile (row `lane` for one warp): its sum
+        // over both warps' columns, then its a_i for the next sweep.
+        const int row = (TE == 64 ? 32 * wt : 0) + lane;
+        const float rsum = TE == 64 ? part[row] + part[TE + row] : v0;
+        arow[row] = row < n ? cS1 - rsum * inv_n_f : -INFINITY;
+      }
+      team_sync<TE>(bar_id);  // every a_i is written
       const bool below = shi < thr_hi || (shi == thr_hi && slo <= thr_lo);
       if (k > 1 && below) break;  // gamma of the last clamped result (reading (iii))
       if (k > a.max_sweeps) break;
