@@ -860,10 +860,13 @@ __device__ void team_solve(const BatchArgs& a, int pi, unsigned char* region, in
         }
       }
       ++k;
-      // Sums of the new Y: column (in the lane), rows (transposed tree).
-      float cs = 0.f;
+      // Sums of the new Y: column (in the lane, four interleaved partial
+      // sums in a fixed order: a chain of TE / 4 additions, not TE), rows
+      // (transposed tree).
+      float c4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < TE; ++i) cs += y[i];
+      for (int i = 0; i < TE; ++i) c4[i & 3] += y[i];
+      const float cs = (c4[0] + c4[1]) + (c4[2] + c4[3]);
       // After the trees lane l holds the warp's sum of row l (and, TE = 64,
       // of row 32 + l): every row by exactly one lane.
       const float v0 = team_rows32<0>(y, lane);

@@ -237,8 +237,9 @@ def test_batched_fp32_one_iteration_matches_oracle(torch_cuda, ctx, variant):
     # not reach at theta = 2 for n >= 16, so both run exactly 10 sweeps.  At
     # n = 10 the first sweep already lands on the doubly stochastic set (no
     # entry is clipped), the oracle's gamma is at FP64 rounding and it stops
-    # after one sweep; FP32 cannot reach 1e-14 there and stops on its
-    # rounding-floor rule within a few sweeps instead, at the same fixed point.
+    # after one sweep.  FP32 stops at the first sweep whose FP32 total falls
+    # to n (1 + 1e-14) or below, which rounding alone decides: anywhere up to
+    # the 10-sweep cap, at the same fixed point (N is checked below).
     torch = torch_cuda
     params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_BF16, max_outer=1,
                                     max_sweeps=10, polish_tol=1e-14)
@@ -256,7 +257,7 @@ def test_batched_fp32_one_iteration_matches_oracle(torch_cuda, ctx, variant):
         if ref.total_sweeps == 10:
             assert inf.total_sweeps == 10
         else:
-            assert ref.total_sweeps == 1 and 1 <= inf.total_sweeps <= 4, (g.n, inf.total_sweeps)
+            assert ref.total_sweeps == 1 and 1 <= inf.total_sweeps <= 10, (g.n, inf.total_sweeps)
         assert err <= 1e-4, (g.n, err)
 
 
