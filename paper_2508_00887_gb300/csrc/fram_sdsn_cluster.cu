@@ -157,6 +157,14 @@ __device__ __forceinline__ float ld_remote_f32(uint32_t addr) {
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
   return v;
 }
+__device__ __forceinline__ float4 ld_remote_f32x4(uint32_t addr) {  // 16-byte aligned
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
 
 // Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -428,34 +436,40 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
       }
       return;
     }
-    // Up to two entries per thread (nr + nc <= 512, 480 threads).
-    int es[2] = {tid - 32, tid - 32 + (kCT - 32)};
-    float v[2][4];
+    // Four consecutive entries per thread (rows [0, nr), then columns
+    // [0, nc)), one 16-byte load from each of the s CTAs that hold partials
+    // of them; each entry is summed in the same fixed order as one at a time.
+    // The partial arrays are 16-byte aligned; entries past nr or nc are
+    // summed from stale words and not stored.
+    const int g = tid - 32;
+    const int rg = (nr + 3) >> 2, cg = (nc + 3) >> 2;
+    if (g < rg + cg) {
+      const bool isrow = g < rg;
+      const int e0 = 4 * (isrow ? g : g - rg);
+      const float* loc = isrow ? &rpub[par * kMaxTile + e0] : &cpub[par * TCP + e0];
+      float4 v[4];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = es[u];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[u][q] = 0.f;
-      if (e < nr) {
-        const float* loc = &rpub[par * kMaxTile + e];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < s) v[u][q] = s > 1 ? ld_remote_f32(remote(loc, (uint32_t)(bi * s + q))) : *loc;
-      } else if (e < nr + nc) {
-        const float* loc = &cpub[par * TCP + (e - nr)];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < s) v[u][q] = s > 1 ? ld_remote_f32(remote(loc, (uint32_t)(q * s + bj))) : *loc;
+      for (int q = 0; q < 4; ++q) {
+        v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < s)
+          v[q] = s > 1 ? ld_remote_f32x4(remote(loc, (uint32_t)(isrow ? bi * s + q : q * s + bj)))
+                       : *reinterpret_cast<const float4*>(loc);
       }
-    }
+      const float acc[4] = {((v[0].x + v[1].x) + v[2].x) + v[3].x,
+                            ((v[0].y + v[1].y) + v[2].y) + v[3].y,
+                            ((v[0].z + v[1].z) + v[2].z) + v[3].z,
+                            ((v[0].w + v[1].w) + v[2].w) + v[3].w};
+      const int lim = isrow ? nr : nc;
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = es[u];
-      const float acc = ((v[u][0] + v[u][1]) + v[u][2]) + v[u][3];
-      if (e < nr)
-        arow[e] = inv_n_f - acc * inv_n_f;
-      else if (e < nr + nc)
-        bcol[e - nr] = acc * inv_n_f;
+      for (int h = 0; h < 4; ++h) {
+        const int e = e0 + h;
+        if (e < lim) {
+          if (isrow)
+            arow[e] = inv_n_f - acc[h] * inv_n_f;
+          else
+            bcol[e] = acc[h] * inv_n_f;
+        }
+      }
     }
   };
 
