@@ -136,7 +136,8 @@ __global__ void lap_rowmax_kernel(const double* __restrict__ W, int ldw, int n, 
     const double* row = W + (size_t)i * ldw;
     double best = -INFINITY, lo = INFINITY;
     int bj = 0x7fffffff;
-    for (int j = lane; j < n; j += 32) {
+#pragma unroll 8
+    for (int j = lane; j < n; j += 32) {  // unrolled: the loads issue together
       const double x = row[j];
       if (x > best) {
         best = x;
@@ -181,6 +182,7 @@ __global__ void lap_colpot_kernel(const double* __restrict__ W, int ldw, int n, 
   const int i0 = blockIdx.y * rows_per, i1 = min(n, i0 + rows_per);
   if (i0 >= i1) return;
   double m = INFINITY;
+#pragma unroll 8
   for (int i = i0; i < i1; ++i) m = fmin(m, w.rowmax[i] - W[(size_t)i * ldw + j]);
   atomicMin(&w.tkey[j], ordered_key(m));
 }
@@ -364,6 +366,7 @@ __global__ void lap_duals_kernel(const double* __restrict__ W, int ldw, int n, L
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     const double* row = W + (size_t)i * ldw;
     double best = -INFINITY;
+#pragma unroll 8
     for (int j = lane; j < n; j += 32) best = fmax(best, row[j] + w.v[j]);
     best = warp_max(best);
     if (lane == 0) {
