@@ -435,9 +435,11 @@ fram_status solve_one(fram_ctx* c, int n, const double* A, const double* B, cons
   if (p.precision == FRAM_PREC_FP64) {
     FR_TRY(prepare_sparse(c, n));
     for (int t = 0; t < p.max_outer; ++t) {
-      FR_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream),
+      // The iteration stats and the max key, adjacent: one memset (the update
+      // kernel rewrites delta and its sums every iteration).
+      FR_CUDA(cudaMemsetAsync(&w.scal->iter, 0, sizeof(IterStats) + sizeof(unsigned long long),
+                              c->stream),
               "memset");
-      FR_CUDA(cudaMemsetAsync(&w.scal->iter.sdsn, 0, sizeof(SdsnStats), c->stream), "memset");
       FR_CUDA(cudaEventRecord(c->evp[0], c->stream), "event");
       FR_TRY(fp64_gradient(c, n, K0 != nullptr, p.lambda, &w.scal->xmax_key));
       FR_CUDA(cudaEventRecord(c->evp[1], c->stream), "event");

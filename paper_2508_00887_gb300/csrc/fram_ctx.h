@@ -17,13 +17,14 @@
 namespace fram {
 
 // Device scalars of one solve.  `lap` and `obj` are adjacent: they are read
-// back with one copy.
+// back with one copy.  `iter` and `xmax_key` are adjacent: the mixed loop
+// clears both with one memset per outer iteration.
 struct DevScalars {
   IterStats iter;
+  unsigned long long xmax_key;
   ValidateStats val;
   LapStats lap;
   ObjStats obj;
-  unsigned long long xmax_key;
   GridBarrier bar;
   unsigned ticket_update;
   unsigned ticket_obj;

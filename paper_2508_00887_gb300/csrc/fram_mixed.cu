@@ -322,10 +322,12 @@ fram_status solve_mixed_loop(fram_ctx* c, int n, bool has_K, const fram_params& 
   const double tol32 = p.polish_tol > p.gamma_tol ? p.polish_tol : p.gamma_tol;
   double prev_delta = INFINITY;
 
+  static_assert(offsetof(DevScalars, xmax_key) == offsetof(DevScalars, iter) + sizeof(IterStats),
+                "iteration stats and max key are cleared together");
   for (int t = 0; t < p.max_outer; ++t) {
-    MX_CUDA(cudaMemsetAsync(&w.scal->xmax_key, 0, sizeof(unsigned long long), c->stream),
+    MX_CUDA(cudaMemsetAsync(&w.scal->iter, 0, sizeof(IterStats) + sizeof(unsigned long long),
+                            c->stream),
             "memset");
-    MX_CUDA(cudaMemsetAsync(&w.scal->iter, 0, sizeof(IterStats), c->stream), "memset");
     MX_CUDA(cudaEventRecord(c->evp[0], c->stream), "event");
     MX_LAUNCH(launch_gemm_tc(b.A, b.Nt, b.T, ld, n, kind, kind == 0 ? 1 : 2, nullptr, 0.0,
                              nullptr, &w.scal->iter.gemm_err, c->wait_limit_ns, c->stream),
