@@ -755,7 +755,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     """DRAM bytes per FP32 SDSN launch (dram__bytes_read.sum +
     dram__bytes_write.sum, one ncu capture of the current kernel), or None
     where no capture covers the size:
-      n = 1000: 4.17 MB per launch, whatever the sweep count: the tiles stay
+      n = 1000: 4.18 MB per launch, whatever the sweep count: the tiles stay
         in shared memory and only X is read (capture of this workload);
       n >= 6144 (the matrix far above L2): 7.80 bytes per element per pass,
         measured at n = 6144 (59.16 GB over 201 passes of 6144^2), scaled to
@@ -763,7 +763,7 @@ def sdsn_traffic(n, s, sweeps_per_launch):
     if s != 4:
         return None
     if n == 1000:
-        return 4.17e6
+        return 4.18e6
     if n >= 6144:
         return 7.80 * n * n * (sweeps_per_launch + 1.0)
     return None

@@ -10,9 +10,11 @@
 // previous sweep, a global all-reduce.  Among co-resident CTAs of a grid that
 // reduction goes through L2 -- a store becomes visible to another SM after
 // about 0.37 us, and among 144 CTAs the exchange costs about 3 us per sweep,
-// more than the sweep's arithmetic.  Within a cluster the partial sums are
-// read from the other CTAs' shared memory (DSMEM) after one hardware cluster
-// barrier (about 0.3 us), so no sweep touches global memory at all.
+// more than the sweep's arithmetic.  Within a cluster each CTA writes its
+// partial sums straight into the shared memory of the CTAs that need them
+// (st.async into distributed shared memory), and each CTA waits on its own
+// mbarrier until every byte it expects has landed, so no sweep touches
+// global memory and no sweep needs a cluster-wide barrier.
 //
 // Layout: CTA (bi, bj) of the s x s cluster owns the tr x tc tile at rows
 // bi*tr, columns bj*tc (tc a multiple of 4).  16 warps; warp w owns tile
@@ -24,12 +26,18 @@
 // Per sweep: the pass updates the tile and accumulates per-lane row and
 // column sums; row sums are reduced across each warp by a transposing
 // shuffle tree, column sums across warps through shared memory, the tile
-// total from the warps' row sums.  The three are published in the CTA's own
-// shared memory (double-buffered by sweep parity), one cluster barrier makes
-// them visible, and every CTA gathers the partials of its rows (from the s
-// CTAs of its tile row), of its columns (s CTAs of its tile column) and all
-// s*s totals, in a fixed order: every CTA forms the same S and gamma, so all
-// of them stop at the same sweep and execute the same cluster barriers.
+// total from the warps' row sums.  Each CTA then pushes its row partials to
+// the s CTAs of its tile row, its column partials to the s CTAs of its tile
+// column and its total to all s*s, into slots indexed by the sender and
+// double-buffered by sweep parity, and waits on that parity's mbarrier for
+// the bytes of all its peers.  It sums the slots in a fixed order: every CTA
+// forms the same S and gamma, so all of them stop at the same sweep.
+//
+// Why two buffers suffice: every CTA sends its tile total to every other
+// CTA, so a CTA that has received all totals of sweep t knows that every
+// CTA has finished sweep t, and with it the reads of the sweep t - 1 slots
+// and the wait on the sweep t - 1 phase of the mbarrier those slots share.
+// Only then does it send its sweep t + 1 partials into them.
 #include <math.h>
 #include <stdint.h>
 
@@ -57,6 +65,7 @@ struct ClusterK {
   int max_sweeps;
   const unsigned long long* xmax_key;
   SdsnStats* stats;
+  uint64_t limit_ns;  // limit of each wait for the peers' partial sums
 };
 
 // Shared-memory layout (floats unless noted), fixed for a kernel variant.
@@ -64,14 +73,14 @@ struct ClusterK {
 // G whole 16-byte groups and every warp 16 rows, so the sweep loop has no
 // bounds tests.  Padding rows carry a_i = -inf and padding columns b_j =
 // +inf; their entries therefore stay 0 and add nothing to any sum.
-//   ts      [kCW * RS][TCP]   tile rows held in shared memory (RS = 16 - RR)
-//   colacc  [kCW][TCP]        per-warp column sums
-//   arow    [kMaxTile]        1/n - r_i/n (-inf on padding rows)
-//   bcol    [TCP]             c_j/n (+inf on padding columns)
-//   rpub    [2][kMaxTile]     published row partials (by sweep parity)
-//   cpub    [2][TCP]          published column partials
-//   wtot    [kCW]             per-warp totals
-//   tpub    [2]               published tile totals
+//   ts      [kCW * RS][TCP]     tile rows held in shared memory (RS = 16 - RR)
+//   colacc  [kCW][TCP]          per-warp column sums
+//   arow    [kMaxTile]          1/n - r_i/n (-inf on padding rows)
+//   bcol    [TCP]               c_j/n (+inf on padding columns)
+//   rrecv   [2][4][kMaxTile]    row partials by sweep parity and sender bj
+//   crecv   [2][4][TCP]         column partials by parity and sender bi
+//   wtot    [kCW]               per-warp totals
+//   trecv   [2][16]             tile totals by parity and sender rank
 template <int G, int RR>
 struct SmemLayout {
   static constexpr int TCP = 128 * G;
@@ -80,11 +89,11 @@ struct SmemLayout {
   static constexpr size_t colacc = ts + (size_t)kCW * RS * TCP * 4;
   static constexpr size_t arow = colacc + (size_t)kCW * TCP * 4;
   static constexpr size_t bcol = arow + (size_t)kMaxTile * 4;
-  static constexpr size_t rpub = bcol + (size_t)TCP * 4;
-  static constexpr size_t cpub = rpub + (size_t)2 * kMaxTile * 4;
-  static constexpr size_t wtot = cpub + (size_t)2 * TCP * 4;
-  static constexpr size_t tpub = wtot + (size_t)kCW * 4;
-  static constexpr size_t bytes = tpub + 2 * 4;
+  static constexpr size_t rrecv = bcol + (size_t)TCP * 4;
+  static constexpr size_t crecv = rrecv + (size_t)2 * 4 * kMaxTile * 4;
+  static constexpr size_t wtot = crecv + (size_t)2 * 4 * TCP * 4;
+  static constexpr size_t trecv = wtot + (size_t)kCW * 4;
+  static constexpr size_t bytes = trecv + 2 * 16 * 4;
 };
 
 // Two FP32 values in one 64-bit register (low word = lower address), and the
@@ -152,18 +161,61 @@ __device__ __forceinline__ uint32_t remote(const void* local, uint32_t rank) {
   return r;
 }
 
-__device__ __forceinline__ float ld_remote_f32(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ float4 ld_remote_f32x4(uint32_t addr) {  // 16-byte aligned
-  float4 v;
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(addr)
+
+// The exchange's mbarriers: one arrival (the owner's, with the byte count it
+// expects) plus the bytes of the peers' st.async stores.  A store may land
+// before the owner arms the phase: the transaction count then runs negative
+// until the owner's expect_tx brings it back.
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes)
                : "memory");
-  return v;
+}
+// Acquire at cluster scope: the peers' st.async stores of the completed
+// phase are visible to the waiting thread afterwards.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of `parity` to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t bar = smem_addr(b);
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (unsigned polls = 1;; ++polls) {
+    if (mbar_test(bar, parity)) return true;
+    if ((polls & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Stores into CTA `rank`'s shared memory that complete on that CTA's
+// mbarrier `bar` (both arguments are local addresses, mapped here).
+__device__ __forceinline__ void push_f32x4(const void* local, float4 v, uint64_t* bar,
+                                           uint32_t rank) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::
+          "r"(remote(local, rank)),
+      "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+      "r"(__float_as_uint(v.w)), "r"(remote(bar, rank))
+      : "memory");
+}
+__device__ __forceinline__ void push_f32(const void* local, float v, uint64_t* bar, uint32_t rank) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                   remote(local, rank)),
+               "r"(__float_as_uint(v)), "r"(remote(bar, rank))
+               : "memory");
 }
 
 // Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
@@ -220,14 +272,16 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
   __shared__ float s_S[2];  // S of the last gathered sweep as hi + lo (double-float)
   __shared__ float s_cS;    // S / n^2 for the next sweep
   __shared__ int s_stop;
+  __shared__ int s_fail;    // a wait for the peers' partials ran out of time
+  __shared__ uint64_t s_bar[2];  // exchange mbarriers, by sweep parity
   float* ts = reinterpret_cast<float*>(smem + Lay::ts);
   float* colacc = reinterpret_cast<float*>(smem + Lay::colacc);
   float* arow = reinterpret_cast<float*>(smem + Lay::arow);
   float* bcol = reinterpret_cast<float*>(smem + Lay::bcol);
-  float* rpub = reinterpret_cast<float*>(smem + Lay::rpub);
-  float* cpub = reinterpret_cast<float*>(smem + Lay::cpub);
+  float* rrecv = reinterpret_cast<float*>(smem + Lay::rrecv);
+  float* crecv = reinterpret_cast<float*>(smem + Lay::crecv);
   float* wtot = reinterpret_cast<float*>(smem + Lay::wtot);
-  float* tpub = reinterpret_cast<float*>(smem + Lay::tpub);
+  float* trecv = reinterpret_cast<float*>(smem + Lay::trecv);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int s = p.s;
@@ -235,6 +289,10 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
   const int bi = (int)rank / s, bj = (int)rank % s;
   const int r0 = bi * p.tr, c0 = bj * p.tc;
   const int nr = max(0, min(p.tr, p.n - r0)), nc = max(0, min(p.tc, p.n - c0));
+  // Partials travel in whole 16-byte groups; a tile row's CTAs share nr and
+  // a tile column's share nc, so sender and receiver count the same groups.
+  const int rg = (nr + 3) >> 2, cg = (nc + 3) >> 2;
+  const uint32_t expect_bytes = (uint32_t)((s - 1) * 16 * (rg + cg) + 4 * (s * s - 1));
 
   // Alg. 2 step 1.  Every CTA reads the same max, so a degenerate input makes
   // all of them return before the first cluster barrier.
@@ -375,12 +433,18 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
     }
   };
 
-  // Reduce the pass's sums and publish them into parity buffer `par`.
-  auto publish = [&](const int par) {
+  // Reduce the pass's sums, keep them in this CTA's own slots of parity
+  // buffer `par` and push them into the same slots of the peers that need
+  // them; then wait until the peers' partials of this sweep have landed.
+  // Returns false when that wait ran out of time.
+  auto publish = [&](const int par, const int t) -> bool {
+    if (s > 1 && tid == 0) mbar_arm(&s_bar[par], expect_bytes);
+    float* rslot = rrecv + (size_t)(par * 4 + bj) * kMaxTile;
+    float* cslot = crecv + (size_t)(par * 4 + bi) * TCP;
     const float rs = transpose_reduce16(racc, lane);
     const int ri = warp + kCW * transpose_index16(lane);
     const bool holder = (lane & 1) == 0 && ri < nr;
-    if (holder) rpub[par * kMaxTile + ri] = rs;
+    if (holder) rslot[ri] = rs;
     const float wt = warp_sum(holder ? rs : 0.f);
     if (lane == 0) wtot[warp] = wt;
 #pragma unroll
@@ -389,22 +453,51 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
           make_ulonglong2(cacc2[g][0], cacc2[g][1]);
     __syncthreads();
     if (tid < TCP) {
+      // Column tid's partial; lanes 4m..4m+3 hand theirs to lane 4m, which
+      // pushes the group to the other CTAs of the tile column.
       float c = 0.f;
 #pragma unroll
       for (int w = 0; w < kCW; ++w) c += colacc[w * TCP + tid];
-      cpub[par * TCP + tid] = c;
-    } else if (tid == TCP || (TCP == kCT && tid == 0)) {
-      float t = 0.f;
+      cslot[tid] = c;
+      if (s > 1) {
+        const float c1 = __shfl_down_sync(0xffffffffu, c, 1);
+        const float c2 = __shfl_down_sync(0xffffffffu, c, 2);
+        const float c3 = __shfl_down_sync(0xffffffffu, c, 3);
+        if ((lane & 3) == 0 && (tid >> 2) < cg) {
+          const float4 v = make_float4(c, c1, c2, c3);
+          for (int q = 0; q < s; ++q)
+            if (q != bi) push_f32x4(&cslot[tid], v, &s_bar[par], (uint32_t)(q * s + bj));
+        }
+      }
+    } else if (tid < TCP + 32) {
+      // The tile total: lane 0 keeps it, lanes 1 .. s*s - 1 push it.
+      float tt = 0.f;
 #pragma unroll
-      for (int w = 0; w < kCW; ++w) t += wtot[w];
-      tpub[par] = t;
+      for (int w = 0; w < kCW; ++w) tt += wtot[w];
+      float* tslot = trecv + par * 16 + rank;
+      if (lane == 0)
+        *tslot = tt;
+      else if (lane < s * s)
+        push_f32(tslot, tt, &s_bar[par], (rank + (uint32_t)lane) % (uint32_t)(s * s));
+    } else if (s > 1) {
+      // Row groups to the other CTAs of the tile row: one group per thread.
+      const int u = tid - (TCP + 32);
+      if (u < (s - 1) * rg) {
+        const int qi = u / rg, e0 = 4 * (u - qi * rg);
+        const int q = qi < bj ? qi : qi + 1;
+        push_f32x4(&rslot[e0], *reinterpret_cast<const float4*>(&rslot[e0]), &s_bar[par],
+                   (uint32_t)(bi * s + q));
+      }
     }
+    __syncthreads();
+    if (s == 1) return true;
+    return mbar_wait(&s_bar[par], (uint32_t)((t >> 1) & 1), p.limit_ns);
   };
 
-  // After the cluster barrier: warp 0 forms S (FP64, from the s*s tile
-  // totals), gamma, S/n^2 and the stop test; the other 15 warps form the
-  // next sweep's row and column terms from the partials of their rows and
-  // columns, each summed over the s CTAs in a fixed order.
+  // After the exchange: warp 0 forms S (from the s*s tile totals), gamma,
+  // S/n^2 and the stop test; the other 15 warps form the next sweep's row
+  // and column terms from the partials of their rows and columns, each
+  // summed over the s senders in a fixed order.
   auto gather = [&](const int par, const int k) {
     if (warp == 0) {
       // S: the s*s tile totals summed as a double-float by a pairwise tree
@@ -412,7 +505,7 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
       // rounding of the low parts, ~2^-48 relative).  A tree, not a chain:
       // the other warps wait for S at the next barrier.
       float hi = 0.f, lo = 0.f;
-      if (lane < s * s) hi = s > 1 ? ld_remote_f32(remote(&tpub[par], (uint32_t)lane)) : tpub[par];
+      if (lane < s * s) hi = trecv[par * 16 + lane];
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         if (o >= s * s) continue;  // uniform: s*s is 1, 4 or 16
@@ -437,23 +530,22 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
       return;
     }
     // Four consecutive entries per thread (rows [0, nr), then columns
-    // [0, nc)), one 16-byte load from each of the s CTAs that hold partials
-    // of them; each entry is summed in the same fixed order as one at a time.
-    // The partial arrays are 16-byte aligned; entries past nr or nc are
-    // summed from stale words and not stored.
+    // [0, nc)), one 16-byte load from each of the s senders' slots; each
+    // entry is summed in the same fixed order as one at a time.  The slots
+    // are 16-byte aligned; entries past nr or nc are summed from stale words
+    // and not stored.
     const int g = tid - 32;
-    const int rg = (nr + 3) >> 2, cg = (nc + 3) >> 2;
     if (g < rg + cg) {
       const bool isrow = g < rg;
       const int e0 = 4 * (isrow ? g : g - rg);
-      const float* loc = isrow ? &rpub[par * kMaxTile + e0] : &cpub[par * TCP + e0];
       float4 v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (q < s)
-          v[q] = s > 1 ? ld_remote_f32x4(remote(loc, (uint32_t)(isrow ? bi * s + q : q * s + bj)))
-                       : *reinterpret_cast<const float4*>(loc);
+          v[q] = *reinterpret_cast<const float4*>(
+              isrow ? &rrecv[(size_t)(par * 4 + q) * kMaxTile + e0]
+                    : &crecv[(size_t)(par * 4 + q) * TCP + e0]);
       }
       const float acc[4] = {((v[0].x + v[1].x) + v[2].x) + v[3].x,
                             ((v[0].y + v[1].y) + v[2].y) + v[3].y,
@@ -473,23 +565,32 @@ __device__ __forceinline__ void sdsn_cluster_body(const ClusterK& p, unsigned ch
     }
   };
 
-  first_pass();
-  publish(0);
+  // The mbarriers must be initialised, and the initialisation visible to
+  // the peers, before the first push.
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   if (s > 1) cluster_sync(); else __syncthreads();
+
+  first_pass();
+  if (!publish(0, 0)) s_fail = 1;
   gather(0, 0);
   __syncthreads();
   int k = 0;
   while (true) {
-    if (s_stop || k >= p.max_sweeps) break;
+    if (s_stop || s_fail || k >= p.max_sweeps) break;
     cS = s_cS;
     sweep_pass();
     ++k;
-    publish(k & 1);
-    if (s > 1) cluster_sync(); else __syncthreads();
+    if (!publish(k & 1, k)) s_fail = 1;
     gather(k & 1, k);
     __syncthreads();
   }
-  // No CTA may leave while another can still read its shared memory.
+  if (s_fail && tid == 0) atomicCAS(&p.stats->status, DEV_OK, DEV_TIMEOUT);
+  // No CTA leaves while a peer may still push into its shared memory.
   if (s > 1) cluster_sync();
 
   // Store the tile.
@@ -572,6 +673,7 @@ bool make_cluster_problem(const SdsnLaunch& L, ClusterK& k) {
   k.max_sweeps = L.max_sweeps;
   k.xmax_key = L.xmax_key;
   k.stats = L.stats;
+  k.limit_ns = L.limit_ns;
   return true;
 }
 

@@ -10,8 +10,8 @@ import bench
 
 def test_sdsn_traffic_measured_and_scaled():
     # n = 1000: the ncu figure, independent of the sweep count (on chip).
-    assert bench.sdsn_traffic(1000, 4, 196.0) == 4.17e6
-    assert bench.sdsn_traffic(1000, 4, 10.0) == 4.17e6
+    assert bench.sdsn_traffic(1000, 4, 196.0) == 4.18e6
+    assert bench.sdsn_traffic(1000, 4, 10.0) == 4.18e6
     # n >= 6144: bytes per element and pass times n^2 (sweeps + 1); at the
     # captured size and sweep count it gives back the capture (59.16 GB).
     t = bench.sdsn_traffic(6144, 4, 200.0)
@@ -53,7 +53,7 @@ def test_cluster_sdsn_roofline_is_alu_on_the_cluster_sms():
     assert r["achieved"] == pytest.approx(5e6 * 2000 / 6.7e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["gpu_frac"] == pytest.approx(r["achieved"] / (152 * 128 * 2.07 / 1e3))
-    assert r["traffic"] == 4.17e6
+    assert r["traffic"] == 4.18e6
     # above the cluster range the FP32 SDSN streams through HBM
     big = SimpleNamespace(**{**vars(info), "ms_sdsn": 490.0})
     assert bench.roofline([big], 8192, "tf32", {"hbm_gbs": 6800.0}, "measured")["bound"] == "hbm"
