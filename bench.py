@@ -795,17 +795,26 @@ def roofline(infos, n, precision, pk, src):
         # exchange on the cluster's SMs, not by HBM: 5 n^2 FP32 operations
         # per sweep (y + a_i, - b_j, the clamp, the row and the column
         # accumulation) against one operation per lane per clock.
+        # Up to n = 64 the iterate sits in the registers of one or two warps
+        # (one scheduler each, 32 lanes): the same count against their lanes.
         side = 1 if n <= 256 else (2 if n <= 512 else 4)
         tc = ((-(-n // side)) + 3) // 4 * 4
         sms = side * side
         clock_ghz = 2.07
         ops = 5.0 * n * n * sweeps
-        sdsn = {"kernel": f"sdsn_cluster_kernel<{'1, 16' if tc <= 128 else '2, 8'}>",
+        if n <= 64:
+            warps = 1 if n <= 32 else 2
+            kernel, lanes = f"sdsn_warp_kernel<{warps}>", warps * 32
+            where = f"the form's {warps} warp{'s' if warps > 1 else ''} x 32 FP32 lanes"
+        else:
+            kernel = f"sdsn_cluster_kernel<{'1, 16' if tc <= 128 else '2, 8'}>"
+            lanes, where = sms * 128, f"the cluster's {sms} SMs x 128 FP32 lanes"
+        sdsn = {"kernel": kernel,
                 "bound": "alu",
                 "achieved": ops / (ms_sdsn / 1e3) / 1e12 if ms_sdsn else None,
-                "peak": sms * 128 * clock_ghz / 1e3, "unit": "TFLOP/s",
-                "peak_source": f"derived: the cluster's {sms} SMs x 128 FP32 lanes x 1 operation "
-                               f"per clock x {clock_ghz} GHz (adds and max, no FMA)",
+                "peak": lanes * clock_ghz / 1e3, "unit": "TFLOP/s",
+                "peak_source": f"derived: {where} x 1 operation per clock x {clock_ghz} GHz "
+                               "(adds and max, no FMA)",
                 "gpu_peak": 152 * 128 * clock_ghz / 1e3,
                 "per_launch_us": 1e3 * ms_sdsn / max(launches, 1),
                 "per_sweep_us": 1e3 * ms_sdsn / max(sweeps, 1)}

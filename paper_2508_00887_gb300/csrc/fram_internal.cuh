@@ -272,15 +272,25 @@ int launch_fra(double* Y, int ldy, double* Yt, int ldt, int n, const unsigned lo
                double theta, double tol, int max_sweeps, double* ws, GridBarrier* bar,
                SdsnStats* stats, uint64_t limit_ns, int num_sms, cudaStream_t s);
 int launch_sdsn_fp64(const SdsnLaunch& L, int num_sms, cudaStream_t s);
-// FP32 SDSN of one problem in one thread-block cluster (2 <= n <= 1024, mode
-// 0, no gate): 1 launched, 0 not applicable (use the grid form), -1 error.
+// FP32 SDSN of one problem on chip (2 <= n <= 1024, mode 0, no gate): one
+// or two warps up to n = 64, one thread-block cluster above.  1 launched, 0
+// not applicable (use the grid form), -1 error.
 int launch_sdsn_cluster(const SdsnLaunch& L, cudaStream_t s);
-// Cluster class of a problem (0: the cluster form does not apply); problems
-// of one class can share one grouped launch, each on its own cluster.
+// On-chip class of a problem, in [0, kSdsnClusterClasses) (0: neither form
+// applies); problems of one class can share one grouped launch, each on its
+// own cluster or CTA.
+constexpr int kSdsnClusterClasses = 9;
 int sdsn_cluster_class(const SdsnLaunch& L);
 int launch_sdsn_cluster_group(const SdsnLaunch* L, int count, void* ddesc, size_t ddesc_bytes,
                               cudaStream_t s);
 size_t sdsn_cluster_desc_bytes();
+// The mixed paths' FP64 polish (FP32 input, mode 1) for 2 <= n <= 64 in one
+// CTA of warps: 1 launched, 0 not applicable (use the grid form), -1 error;
+// and many such polishes at once (every problem must apply).
+int launch_sdsn_polish_small(const SdsnLaunch& L, cudaStream_t s);
+int launch_sdsn_polish_small_group(const SdsnLaunch* L, int count, void* ddesc,
+                                   size_t ddesc_bytes, cudaStream_t s);
+bool sdsn_polish_small_applies(const SdsnLaunch& L);
 int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s);
 // Several problems (same precision pair) in one cooperative launch of at most
 // max_blocks CTAs; ddesc is device scratch of sdsn_group_desc_bytes(count).

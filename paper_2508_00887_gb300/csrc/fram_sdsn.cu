@@ -786,7 +786,12 @@ int launch_sdsn(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
     if (k != 0) return k;
     return launch_sdsn_t<float, float>(L, num_sms, s);
   }
-  if (L.in_fp32 && !L.out_fp32) return launch_sdsn_t<double, float>(L, num_sms, s);
+  if (L.in_fp32 && !L.out_fp32) {
+    // The mixed paths' FP64 polish of a small problem: one CTA of warps.
+    const int k = launch_sdsn_polish_small(L, s);
+    if (k != 0) return k;
+    return launch_sdsn_t<double, float>(L, num_sms, s);
+  }
   return -1;
 }
 

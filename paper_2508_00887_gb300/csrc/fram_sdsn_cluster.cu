@@ -229,32 +229,33 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // holds the total of entry ((l >> 4) & 1) * 8 + ((l >> 3) & 1) * 4 +
 // ((l >> 2) & 1) * 2 + ((l >> 1) & 1), and lanes l, l ^ 1 hold the same one.
 // 16 shuffles instead of 80; the addition order is fixed.
-__device__ __forceinline__ float transpose_reduce16(float (&v)[16], int lane) {
+template <typename T>
+__device__ __forceinline__ T transpose_reduce16(T (&v)[16], int lane) {
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const bool hi = lane & 16;
-    const float send = hi ? v[m] : v[m + 8];
-    const float keep = hi ? v[m + 8] : v[m];
+    const T send = hi ? v[m] : v[m + 8];
+    const T keep = hi ? v[m + 8] : v[m];
     v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     const bool hi = lane & 8;
-    const float send = hi ? v[m] : v[m + 4];
-    const float keep = hi ? v[m + 4] : v[m];
+    const T send = hi ? v[m] : v[m + 4];
+    const T keep = hi ? v[m + 4] : v[m];
     v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     const bool hi = lane & 4;
-    const float send = hi ? v[m] : v[m + 2];
-    const float keep = hi ? v[m + 2] : v[m];
+    const T send = hi ? v[m] : v[m + 2];
+    const T keep = hi ? v[m + 2] : v[m];
     v[m] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
   {
     const bool hi = lane & 2;
-    const float send = hi ? v[0] : v[1];
-    const float keep = hi ? v[1] : v[0];
+    const T send = hi ? v[0] : v[1];
+    const T keep = hi ? v[1] : v[0];
     v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
@@ -649,6 +650,357 @@ __global__ void __launch_bounds__(kCT, 1) sdsn_cluster_group_kernel(const Cluste
   sdsn_cluster_body<G, RR>(p, smem);
 }
 
+// ---------------------------------------------------------------------------
+// Small problems, 2 <= n <= 64: the warp form.  NC warps of 32 threads; warp
+// w owns rows 32w .. 32w + 31 and lane l owns columns l + 32c (c < NC), so
+// the whole iterate stays in the lanes' registers.  A sweep forms each row's
+// sum with one transposed shuffle tree over the warp's 32 rows and each
+// column's sum in the lane that owns it.  With two warps the two column
+// halves meet in shared memory behind one 64-thread barrier, double-buffered
+// by sweep parity: that is the sweep's only barrier.  Every lane forms S (a
+// double-float tree over the column sums), gamma and the stop test itself,
+// with the same operations, so all lanes take the same branch.
+// ---------------------------------------------------------------------------
+
+// Sum of v[0..31] over the 32 lanes, transposed: afterwards lane l holds the
+// total of entry l.  31 shuffles, in a fixed order.  (Arithmetic of the warp
+// form is written with _rn intrinsics so that no two kernels built from it
+// can differ by a contraction into FMA: the grouped launch must reproduce
+// the solo one bit for bit.)
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool hi = lane & h;
+#pragma unroll
+    for (int m = 0; m < h; ++m) {
+      const float send = hi ? v[m] : v[m + h];
+      const float keep = hi ? v[m + h] : v[m];
+      v[m] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
+template <int NC>
+__device__ __forceinline__ void sdsn_warp_body(const ClusterK& p) {
+  __shared__ float s_a[NC][32];               // 1/n - r_i/n of each warp's rows
+  __shared__ float s_colp[2][NC][32 * NC];    // column partials by parity and warp
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = p.n, r0 = 32 * w;
+
+  // Alg. 2 step 1 (every thread reads the same max).
+  const double m = from_ordered_key(*p.xmax_key);
+  if (!(m > 0.0)) {
+    if (threadIdx.x == 0) {
+      p.stats->status = DEV_DEGENERATE;
+      p.stats->sweeps = 0;
+      p.stats->converged = 0;
+      p.stats->gamma = INFINITY;
+      p.stats->xmax = m;
+    }
+    return;
+  }
+  const double n_d = (double)n;
+  const double inv_n = 1.0 / n_d;
+  const float inv_n_f = (float)inv_n, inv_n2_f = (float)(inv_n * inv_n);
+  const float scale = (float)((p.theta / 2.0) / m);
+  const double thr = n_d * (1.0 + p.gamma_tol);
+  const float thr_hi = (float)thr, thr_lo = (float)(thr - (double)thr_hi);
+
+  float y[32][NC];  // rows r0 + r, columns lane + 32c
+  float rp[32];     // this lane's part of each row sum
+  float cacc[NC];   // this lane's column sums
+  float bb[NC];     // c_j/n (+inf on padding columns)
+  float cS = 0.f, S_hi = 0.f, S_lo = 0.f;
+
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cacc[c] = 0.f;
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int i = r0 + r;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int j = lane + 32 * c;
+      const float v = (i < n && j < n) ? __fmul_rn(p.X[(size_t)i * p.ldx + j], scale) : 0.f;
+      y[r][c] = v;
+      rp[r] = c == 0 ? v : __fadd_rn(rp[r], v);
+      cacc[c] = __fadd_rn(cacc[c], v);
+    }
+  }
+
+  // The sums of the pass just made: the next sweep's a_i (in s_a) and b_j,
+  // S/n^2, and the stop test after sweep k.
+  auto exchange = [&](const int par, const int k) -> bool {
+    // Column totals first: the barrier's wait then overlaps nothing that
+    // matters, and the row tree below is independent of the S tree, so the
+    // two interleave.
+    float ct[NC];
+    if constexpr (NC == 1) {
+      ct[0] = cacc[0];
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s_colp[par][w][lane + 32 * c] = cacc[c];
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        ct[c] = __fadd_rn(s_colp[par][0][lane + 32 * c], s_colp[par][1][lane + 32 * c]);
+    }
+    const float rs = transpose_reduce32(rp, lane);  // row r0 + lane
+#pragma unroll
+    for (int c = 0; c < NC; ++c) bb[c] = lane + 32 * c < n ? __fmul_rn(ct[c], inv_n_f) : INFINITY;
+    __syncwarp();
+    s_a[w][lane] = r0 + lane < n ? __fmaf_rn(-rs, inv_n_f, inv_n_f) : -INFINITY;
+    __syncwarp();
+    // S over all columns: a pairwise double-float butterfly.  TwoSum is
+    // exact, so lanes l and l ^ o form the same pair and every lane (of
+    // either warp) ends with the same S.
+    float hi = ct[0], lo = 0.f;
+#pragma unroll
+    for (int c = 1; c < NC; ++c) {
+      float e;
+      two_sum(hi, ct[c], hi, e);
+      lo += e;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+      float e;
+      two_sum(hi, ohi, hi, e);
+      lo = (lo + olo) + e;
+    }
+    {
+      float e;
+      two_sum(hi, lo, hi, e);
+      lo = e;
+    }
+    S_hi = hi;
+    S_lo = lo;
+    cS = __fmaf_rn(hi, inv_n2_f, __fmul_rn(lo, inv_n2_f));
+    const bool below = hi < thr_hi || (hi == thr_hi && lo <= thr_lo);
+    return k > 0 && below;
+  };
+
+  bool stop = exchange(0, 0);
+  int k = 0;
+  while (!stop && k < p.max_sweeps) {
+    // The fused P1 + P2 sweep (eq. 7).
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cacc[c] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const float ai = __fadd_rn(s_a[w][r], cS);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float t = fmaxf(__fsub_rn(__fadd_rn(y[r][c], ai), bb[c]), 0.f);
+        y[r][c] = t;
+        rp[r] = c == 0 ? t : __fadd_rn(rp[r], t);
+        cacc[c] = __fadd_rn(cacc[c], t);
+      }
+    }
+    ++k;
+    stop = exchange(k & 1, k);
+  }
+
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int i = r0 + r;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int j = lane + 32 * c;
+      if (i < n && j < n) p.Y[(size_t)i * p.ldy + j] = y[r][c];
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double g = k > 0 ? ((double)S_hi + (double)S_lo) * inv_n - 1.0 : INFINITY;
+    p.stats->sweeps = k;
+    p.stats->gamma = g;
+    p.stats->converged = (g <= p.gamma_tol) ? 1 : 0;
+    p.stats->xmax = m;
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(32 * NC) sdsn_warp_kernel(const __grid_constant__ ClusterK p) {
+  sdsn_warp_body<NC>(p);
+}
+
+// Problem b of a group in CTA b: each CTA computes exactly what the solo
+// launch computes for its problem.
+template <int NC>
+__global__ void __launch_bounds__(32 * NC) sdsn_warp_group_kernel(const ClusterK* probs) {
+  sdsn_warp_body<NC>(probs[blockIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// The FP64 polish of the mixed paths for 2 <= n <= 64, in the same form: it
+// continues from the FP32 result (Y0 = X, no scaling) and runs FP64 sweeps
+// until gamma <= gamma_tol or max_sweeps, or none at all when the gate says
+// the FP32 phase already met its tolerance.  2 NC warps of 16 rows each, so
+// that all four schedulers' FP64 units work; lane l owns columns l + 32c.
+// Row sums by one transposed shuffle tree per warp, column sums through
+// shared memory behind one barrier per sweep (double-buffered by parity), S
+// by a butterfly over the column sums, identical in every lane.
+// ---------------------------------------------------------------------------
+struct PolishK {
+  int n;
+  const float* X;
+  int ldx;
+  double* Y;
+  int ldy;
+  double gamma_tol;
+  int max_sweeps;
+  const SdsnStats* gate;
+  double gate_tol;
+  SdsnStats* stats;
+};
+
+// max(0, y) on the integer pipe: clear y if its sign bit is set.
+__device__ __forceinline__ double relu_d(double y) {
+  const long long b = __double_as_longlong(y);
+  return __longlong_as_double(b & ~(b >> 63));
+}
+
+template <int NC>
+__device__ __forceinline__ void polish_warp_body(const PolishK& p) {
+  constexpr int W = 2 * NC;
+  __shared__ double s_a[W][16];
+  __shared__ double s_colp[2][W][32 * NC];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n = p.n, r0 = 16 * w;
+  const int max_sweeps =
+      (p.gate != nullptr && p.gate->gamma <= p.gate_tol) ? 0 : p.max_sweeps;
+  const double inv_n = 1.0 / (double)n, inv_n2 = inv_n * inv_n;
+
+  double y[16][NC], rp[16], cacc[NC], bb[NC];
+  double cS = 0.0, g = INFINITY;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cacc[c] = 0.0;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = r0 + r;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int j = lane + 32 * c;
+      const double v = (i < n && j < n) ? (double)p.X[(size_t)i * p.ldx + j] : 0.0;
+      y[r][c] = v;
+      rp[r] = c == 0 ? v : __dadd_rn(rp[r], v);
+      cacc[c] = __dadd_rn(cacc[c], v);
+    }
+  }
+
+  // Sums of the pass just made; returns the stop test (gamma of this pass;
+  // as a continuation, the input itself may already meet the tolerance).
+  auto exchange = [&](const int par) -> bool {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s_colp[par][w][lane + 32 * c] = cacc[c];
+    __syncthreads();
+    double ct[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double t = s_colp[par][0][lane + 32 * c];
+#pragma unroll
+      for (int q = 1; q < W; ++q) t = __dadd_rn(t, s_colp[par][q][lane + 32 * c]);
+      ct[c] = t;
+    }
+    const double rs = transpose_reduce16(rp, lane);  // row r0 + (lane >> 1)
+    double S = ct[0];
+#pragma unroll
+    for (int c = 1; c < NC; ++c) S = __dadd_rn(S, ct[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) S = __dadd_rn(S, __shfl_xor_sync(0xffffffffu, S, o));
+#pragma unroll
+    for (int c = 0; c < NC; ++c) bb[c] = lane + 32 * c < n ? __dmul_rn(ct[c], inv_n) : INFINITY;
+    __syncwarp();
+    const int ri = lane >> 1;
+    if ((lane & 1) == 0) s_a[w][ri] = r0 + ri < n ? __fma_rn(-rs, inv_n, inv_n) : -INFINITY;
+    __syncwarp();
+    cS = __dmul_rn(S, inv_n2);
+    g = __fma_rn(S, inv_n, -1.0);
+    return g <= p.gamma_tol;
+  };
+
+  bool stop = exchange(0);
+  int k = 0;
+  while (!stop && k < max_sweeps) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cacc[c] = 0.0;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const double ai = __dadd_rn(s_a[w][r], cS);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double t = relu_d(__dsub_rn(__dadd_rn(y[r][c], ai), bb[c]));
+        y[r][c] = t;
+        rp[r] = c == 0 ? t : __dadd_rn(rp[r], t);
+        cacc[c] = __dadd_rn(cacc[c], t);
+      }
+    }
+    ++k;
+    stop = exchange(k & 1);
+  }
+
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = r0 + r;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int j = lane + 32 * c;
+      if (i < n && j < n) p.Y[(size_t)i * p.ldy + j] = y[r][c];
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.stats->sweeps = k;
+    p.stats->gamma = g;
+    p.stats->converged = (g <= p.gamma_tol) ? 1 : 0;
+    p.stats->xmax = 1.0;
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(64 * NC) polish_warp_kernel(const __grid_constant__ PolishK p) {
+  polish_warp_body<NC>(p);
+}
+
+template <int NC>
+__global__ void __launch_bounds__(64 * NC) polish_warp_group_kernel(const PolishK* probs) {
+  polish_warp_body<NC>(probs[blockIdx.x]);
+}
+
+// Warps (and columns per lane) of the warp form for n, 0 above 64.
+int warp_form(int n) { return n <= 32 ? 1 : n <= 64 ? 2 : 0; }
+
+bool polish_warp_applies(const SdsnLaunch& L) {
+  return L.in_fp32 && !L.out_fp32 && L.mode == 1 && L.n >= 2 && L.n <= 64;
+}
+
+PolishK make_polish(const SdsnLaunch& L) {
+  PolishK k{};
+  k.n = L.n;
+  k.X = static_cast<const float*>(L.X);
+  k.ldx = L.ldx;
+  k.Y = static_cast<double*>(L.Y);
+  k.ldy = L.ldy;
+  k.gamma_tol = L.gamma_tol;
+  k.max_sweeps = L.max_sweeps;
+  k.gate = L.gate;
+  k.gate_tol = L.gate_tol;
+  k.stats = L.stats;
+  return k;
+}
+
+int launch_warp_form(const ClusterK* dk, const ClusterK* hk, int count, cudaStream_t st) {
+  const int nc = warp_form(hk[0].n);
+  if (dk == nullptr) {
+    if (nc == 1) sdsn_warp_kernel<1><<<1, 32, 0, st>>>(hk[0]);
+    else sdsn_warp_kernel<2><<<1, 64, 0, st>>>(hk[0]);
+  } else {
+    if (nc == 1) sdsn_warp_group_kernel<1><<<count, 32, 0, st>>>(dk);
+    else sdsn_warp_group_kernel<2><<<count, 64, 0, st>>>(dk);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 // Cluster side s for n: one CTA up to 256, 2 x 2 up to 512, 4 x 4 up to 1024.
 int cluster_side(int n) { return n <= 256 ? 1 : n <= 512 ? 2 : 4; }
 
@@ -756,17 +1108,19 @@ size_t problem_smem(const ClusterK& k) {
 int launch_sdsn_cluster(const SdsnLaunch& L, cudaStream_t st) {
   ClusterK k;
   if (!make_cluster_problem(L, k)) return 0;
+  if (warp_form(k.n)) return launch_warp_form(nullptr, &k, 1, st);
   const size_t smem = problem_smem(k);
   if (k.tc <= 128) return launch_cluster_t<1, 16>(nullptr, &k, 1, smem, st);
   return launch_cluster_t<2, 8>(nullptr, &k, 1, smem, st);
 }
 
 // Cluster class of a problem (problems of one class can share a grouped
-// launch): 1 + 3 * (wide tile) + (side index), 0 if the cluster form does
-// not apply.
+// launch): 1 + 3 * (wide tile) + (side index) for the cluster forms, 6 +
+// (warps) for the warp form, 0 if neither applies.
 int sdsn_cluster_class(const SdsnLaunch& L) {
   ClusterK k;
   if (!make_cluster_problem(L, k)) return 0;
+  if (const int nw = warp_form(k.n)) return 6 + nw;
   const int si = k.s == 1 ? 0 : k.s == 2 ? 1 : 2;
   return 1 + 3 * (k.tc > 128 ? 1 : 0) + si;
 }
@@ -781,7 +1135,9 @@ int launch_sdsn_cluster_group(const SdsnLaunch* L, int count, void* ddesc, size_
   size_t smem = 0;
   for (int i = 0; i < count; ++i) {
     if (!make_cluster_problem(L[i], ks[i])) return -1;
-    if (ks[i].s != ks[0].s || (ks[i].tc > 128) != (ks[0].tc > 128)) return -1;
+    if (ks[i].s != ks[0].s || (ks[i].tc > 128) != (ks[0].tc > 128) ||
+        warp_form(ks[i].n) != warp_form(ks[0].n))
+      return -1;
     const size_t b = problem_smem(ks[i]);
     smem = b > smem ? b : smem;
   }
@@ -790,11 +1146,52 @@ int launch_sdsn_cluster_group(const SdsnLaunch* L, int count, void* ddesc, size_
       cudaSuccess)
     return -1;
   const ClusterK* dk = static_cast<const ClusterK*>(ddesc);
+  if (warp_form(ks[0].n)) return launch_warp_form(dk, ks.data(), count, st);
   const int r = ks[0].tc <= 128 ? launch_cluster_t<1, 16>(dk, ks.data(), count, smem, st)
                                 : launch_cluster_t<2, 8>(dk, ks.data(), count, smem, st);
   return r == 0 ? -1 : r;
 }
 
 size_t sdsn_cluster_desc_bytes() { return sizeof(ClusterK); }
+
+bool sdsn_polish_small_applies(const SdsnLaunch& L) { return polish_warp_applies(L); }
+
+// FP64 polish of one problem with 2 <= n <= 64 in the warp form: 1 launched,
+// 0 not applicable (the caller uses the grid form), -1 error.
+int launch_sdsn_polish_small(const SdsnLaunch& L, cudaStream_t st) {
+  if (!polish_warp_applies(L)) return 0;
+  const PolishK k = make_polish(L);
+  if (warp_form(k.n) == 1)
+    polish_warp_kernel<1><<<1, 64, 0, st>>>(k);
+  else
+    polish_warp_kernel<2><<<1, 128, 0, st>>>(k);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// `count` such polishes in at most two launches (one per warp form), each
+// CTA computing exactly what launch_sdsn_polish_small computes for its
+// problem.  ddesc: device scratch of count * sdsn_cluster_desc_bytes().
+int launch_sdsn_polish_small_group(const SdsnLaunch* L, int count, void* ddesc,
+                                   size_t ddesc_bytes, cudaStream_t st) {
+  if (count < 1) return 0;
+  std::vector<PolishK> ks;
+  ks.reserve(count);
+  int n1 = 0;
+  for (int form = 1; form <= 2; ++form)
+    for (int i = 0; i < count; ++i) {
+      if (!polish_warp_applies(L[i])) return -1;
+      if (warp_form(L[i].n) != form) continue;
+      ks.push_back(make_polish(L[i]));
+      if (form == 1) ++n1;
+    }
+  if (ks.size() * sizeof(PolishK) > ddesc_bytes) return -1;
+  if (cudaMemcpyAsync(ddesc, ks.data(), ks.size() * sizeof(PolishK), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return -1;
+  const PolishK* dk = static_cast<const PolishK*>(ddesc);
+  if (n1 > 0) polish_warp_group_kernel<1><<<n1, 64, 0, st>>>(dk);
+  if (count - n1 > 0) polish_warp_group_kernel<2><<<count - n1, 128, 0, st>>>(dk + n1);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 }  // namespace fram

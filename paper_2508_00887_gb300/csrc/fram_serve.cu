@@ -395,21 +395,31 @@ void serve_loop(fram_ctx* c, Serve* Sp) {
       }
     };
     waves(L64);
-    // FP32 problems of 2 <= n <= 1024 run on one cluster each, as fram_solve
-    // runs them: one launch per cluster class, any number of problems.
+    // FP32 problems of 2 <= n <= 1024 run on chip, as fram_solve runs them
+    // (warps up to n = 64, one cluster each above): one launch per class,
+    // any number of problems.
     {
-      std::vector<SdsnLaunch> grid32, cls[7];
+      std::vector<SdsnLaunch> grid32, cls[kSdsnClusterClasses];
       for (const SdsnLaunch& L : L32) {
         const int k = sdsn_cluster_class(L);
         (k > 0 ? cls[k] : grid32).push_back(L);
       }
-      for (int k = 1; k < 7 && ok; ++k)
+      for (int k = 1; k < kSdsnClusterClasses && ok; ++k)
         if (!cls[k].empty())
           ok = SV_OK(launch_sdsn_cluster_group(cls[k].data(), (int)cls[k].size(), S.ddesc, dbytes,
                                                s)) && ok;
       waves(grid32);
     }
-    waves(Lpol);
+    // FP64 polishes: those of 2 <= n <= 64 in one CTA of warps each, as
+    // fram_solve runs them; the rest in co-resident waves.
+    {
+      std::vector<SdsnLaunch> small, rest;
+      for (const SdsnLaunch& L : Lpol) (sdsn_polish_small_applies(L) ? small : rest).push_back(L);
+      if (!small.empty())
+        ok = SV_OK(launch_sdsn_polish_small_group(small.data(), (int)small.size(), S.ddesc, dbytes,
+                                                  s)) && ok;
+      waves(rest);
+    }
     // Steps 7-8: one grouped update per precision (FP64 requests alone).
     std::vector<UpdGroupProblem> up[2];
     for (Request* r : act) {

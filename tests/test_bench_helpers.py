@@ -54,6 +54,15 @@ def test_cluster_sdsn_roofline_is_alu_on_the_cluster_sms():
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["gpu_frac"] == pytest.approx(r["achieved"] / (152 * 128 * 2.07 / 1e3))
     assert r["traffic"] == 4.18e6
+    # n = 50: the two-warp form, against its 64 lanes
+    small = SimpleNamespace(**{**vars(info), "ms_sdsn": 0.8, "total_sweeps": 1393,
+                               "polish_sweeps": 24, "outer_iters": 8})
+    rs = bench.roofline([small], 50, "tf32", {"hbm_gbs": 6800.0}, "measured")
+    assert rs["bound"] == "alu" and rs["kernel"] == "sdsn_warp_kernel<2>"
+    assert rs["peak"] == pytest.approx(64 * 2.07 / 1e3)
+    assert rs["achieved"] == pytest.approx(5 * 2500 * 1369 / 0.8e-3 / 1e12)
+    assert bench.roofline([small], 20, "tf32", {"hbm_gbs": 6800.0},
+                          "measured")["kernel"] == "sdsn_warp_kernel<1>"
     # above the cluster range the FP32 SDSN streams through HBM
     big = SimpleNamespace(**{**vars(info), "ms_sdsn": 490.0})
     assert bench.roofline([big], 8192, "tf32", {"hbm_gbs": 6800.0}, "measured")["bound"] == "hbm"

@@ -146,13 +146,15 @@ def test_mixed_dense_gaussian_equal_accuracy(torch_cuda, ctx):
     assert err <= X_TOL[fr.FRAM_PREC_MIXED_BF16]
 
 
-def test_mixed_polish_reaches_fp64_tolerance(torch_cuda, ctx):
+@pytest.mark.parametrize("n", [24, 40, 120])
+def test_mixed_polish_reaches_fp64_tolerance(torch_cuda, ctx, n):
     # theta = 2 on a small dense pair, where SDSN converges.  (1) The FP32
     # phase reaches polish_tol, so the gate skips the FP64 polish.  (2) With
     # the FP32 phase capped at 3 sweeps, gamma is still large, the polish runs
-    # and takes gamma to gamma_tol in FP64.
+    # and takes gamma to gamma_tol in FP64.  n = 24 and 40 run the polish in
+    # its warp forms (one CTA of 2 or 4 warps), n = 120 in the grid form.
     torch = torch_cuda
-    g = fi.gaussian_pair(120, jitter=0.01, seed=4)
+    g = fi.gaussian_pair(n, jitter=0.01, seed=4)
     n = g.n
     A = torch.from_numpy(g.A).cuda()
     B = torch.from_numpy(g.B).cuda()

@@ -11,8 +11,9 @@ Covered variants (the grid and tile follow from n alone):
     iterate resident in L2 (six groups per lane);
   * n = 8192, stride 8192: the dense workload's size, 256 MB iterate
     streamed from HBM every sweep (six groups per lane);
-  * small and ragged sizes: the one-CTA cluster form (n <= 256), odd n and
-    unaligned strides.
+  * small and ragged sizes: the warp forms (one warp for n <= 32, two for
+    n <= 64, the boundaries on both sides), the one-CTA cluster form
+    (n <= 256), odd n and unaligned strides.
 
 Tolerance, derived from the arithmetic.  The oracle runs the same sweeps in
 FP64 on the same (FP32-representable) input.  P1 (an affine projection) and
@@ -22,7 +23,7 @@ sweeps ||D32 - D64||_F is at most the sum of the rounding errors each sweep
 adds.  Per element a sweep rounds y + a_i, then - b_j (a_i = 1/n + S/n^2 -
 r_i/n, b_j = c_j/n), and a_i, b_j carry the FP32 rounding of 1/n, of the
 products and of the row/column sums (at most 64 sequential additions deep
-in every grid this library picks).  Summed in the Frobenius norm over the
+in every grid this library picks; 33 in the warp forms).  Summed in the Frobenius norm over the
 matrix, sweep t adds at most
     u (2 ||Y_t|| + 3 sqrt(n) ||a_t|| + 2 sqrt(n) ||b_t||
        + 64 sqrt(n) (||r_t|| + ||c_t||) / n),          u = 2^-24,
@@ -34,8 +35,10 @@ large next to the entries).  A structural slip (a dropped or mis-signed term,
 a transposed or misplaced partial, a skipped sweep) gives O(1) errors.
 gamma = S/n - 1: |gamma32 - gamma64| <= ||D32 - D64||_F (Cauchy-Schwarz over
 n^2 entries, divided by n) plus the FP32 rounding of S, 64 u (1 + gamma).
-The sweep count is fixed (gamma_tol = 0) wherever D is compared, so that
-FP32 rounding cannot move the stop by a sweep.
+The sweep count is fixed wherever D is compared, so that FP32 rounding
+cannot move the stop by a sweep: gamma_tol = -1, below any gamma (gamma >= 0
+after the clamp, up to rounding).  With gamma_tol = 0 a one-sweep-exact case
+(n = 2) stops at gamma = -1e-16 in FP64 and one sweep later in FP32.
 """
 import numpy as np
 import pytest
@@ -48,6 +51,7 @@ pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
 SUM_DEPTH = 64
+FIXED = -1.0  # a gamma_tol no sweep reaches
 
 
 @pytest.fixture(scope="module")
@@ -124,7 +128,14 @@ CASES = [
     (2800, 2816, 8, 10.0, "skewed"),
     (4039, 4096, 8, 10.0, "skewed"),
     (8192, 8192, 4, 2.0, "skewed"),
+    (2, 2, 10, 2.0, "skewed"),
+    (10, 13, 10, 10.0, "skewed"),
+    (31, 31, 12, 2.0, "skewed"),
+    (32, 36, 10, 10.0, "gradient"),
+    (33, 33, 10, 2.0, "skewed"),
     (50, 50, 10, 10.0, "gradient"),
+    (64, 64, 10, 10.0, "gradient"),
+    (65, 67, 10, 2.0, "skewed"),
     (97, 101, 10, 2.0, "skewed"),
     (333, 333, 10, 10.0, "skewed"),
 ]
@@ -133,8 +144,8 @@ CASES = [
 @pytest.mark.parametrize("n,ld,sweeps,theta,kind", CASES)
 def test_sdsn_f32_matches_oracle(torch_cuda, ctx, n, ld, sweeps, theta, kind):
     X = gradient_input(n, 3) if kind == "gradient" else skewed_input(n, n + ld)
-    ref = o.sdsn(X, theta, 0.0, sweeps)
-    D, pad, k, g = run_f32(torch_cuda, ctx, X, ld, theta, 0.0, sweeps)
+    ref = o.sdsn(X, theta, FIXED, sweeps)
+    D, pad, k, g = run_f32(torch_cuda, ctx, X, ld, theta, FIXED, sweeps)
     dist = float(np.linalg.norm(D - ref.D))
     bound = fp32_bound(X, theta, sweeps)
     print(f"n={n} ld={ld} sweeps={k} relF={dist / np.linalg.norm(ref.D):.3e} "
@@ -160,16 +171,17 @@ def test_sdsn_f32_in_place_equals_out_of_place(torch_cuda, ctx, n, ld):
     assert np.all(pad == 7.0)
 
 
-def test_sdsn_f32_stops_at_gamma_tol(torch_cuda, ctx):
+@pytest.mark.parametrize("n", [24, 40, 200])
+def test_sdsn_f32_stops_at_gamma_tol(torch_cuda, ctx, n):
     # theta = 2 on a small dense input converges: the FP32 run stops at its
     # first sweep k with gamma32 <= tol.  gamma32 is within eps of the exact
     # gamma of that sweep (eps: the D bound plus the FP32 rounding of S, as in
     # the module docstring), so the exact gamma at the FP32 stop is at most
     # tol + eps, and every earlier sweep's exact gamma is above tol - eps.
-    n = 200
+    # n = 24 and 40 run the warp forms, n = 200 the one-CTA cluster.
     X = skewed_input(n, 5)
     tol = 1e-6
-    ref = o.sdsn(X, 2.0, 0.0, 2000, keep_history=True)
+    ref = o.sdsn(X, 2.0, FIXED, 2000, keep_history=True)
     D, _, k, g = run_f32(torch_cuda, ctx, X, n, 2.0, tol, 2000)
     hist = np.array(ref.gammas)
     eps = fp32_bound(X, 2.0, k) + SUM_DEPTH * U32 * (1.0 + tol)
