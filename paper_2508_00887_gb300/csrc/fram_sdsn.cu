@@ -58,6 +58,7 @@ struct SdsnK {
   double* tpart;  // [2][P*Q] tile totals (S and gamma are always FP64)
   GridBarrier* bar;
   uint64_t limit_ns;
+  double one;  // 1.0, read at run time (see addx)
 };
 
 template <typename T>
@@ -81,6 +82,13 @@ __device__ __forceinline__ float relu(float y) {
   const int b = __float_as_int(y);
   return __int_as_float(b & ~(b >> 31));
 }
+
+// Sweep additions: FP64 ones as fma with a run-time 1.0 (add64, exact and
+// faster on this GPU's FP64 pipe), FP32 ones plain.
+__device__ __forceinline__ double addx(double a, double b, double one) { return add64(a, b, one); }
+__device__ __forceinline__ double subx(double a, double b, double one) { return sub64(a, b, one); }
+__device__ __forceinline__ float addx(float a, float b, double) { return a + b; }
+__device__ __forceinline__ float subx(float a, float b, double) { return a - b; }
 
 // Sum of v[0..7] over the 32 lanes of a warp, transposed: afterwards lane l
 // holds the total of entry ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 +
@@ -171,23 +179,24 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
                                           int nc, int r0, int c0, int bi, int bj, T scale, int wb,
                                           int blk, int nblk, T cS, T inv_n_t, double* s_total) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double one = p.one;
   T* wacc = colacc + warp * p.tc;
   if constexpr (MAXC == 0) {
     for (int j = lane; j < nc; j += 32) wacc[j] = T(0);
     for (int i = warp; i < nr; i += kSdsnWarps) {
       T* row = tile + (size_t)i * ldt;
       const TIn* xrow = FIRST ? p.X + (size_t)(r0 + i) * p.ldx + c0 : nullptr;
-      const T ai = FIRST ? T(0) : arow[i] + cS;
+      const T ai = FIRST ? T(0) : addx(arow[i], cS, one);
       T racc = T(0);
       for (int j = lane; j < nc; j += 32) {
         T y;
         if (FIRST)
           y = p.mode == 0 ? (T)xrow[j] * scale : (T)xrow[j];
         else
-          y = relu((row[j] + ai) - bcol[j]);
+          y = relu(subx(addx(row[j], ai, one), bcol[j], one));
         row[j] = y;
-        racc += y;
-        wacc[j] += y;
+        racc = addx(racc, y, one);
+        wacc[j] = addx(wacc[j], y, one);
       }
       racc = warp_sum(racc);
       if (lane == 0) rowsum[i] = racc;
@@ -224,7 +233,7 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
     // lane's part of the row sum.
     auto do_row = [&](int i, T (&src)[MAXC][VEC]) {
       T* row = tile + (size_t)i * ldt;
-      const T ai = FIRST ? T(0) : arow[i] + cS;
+      const T ai = FIRST ? T(0) : addx(arow[i], cS, one);
       T racc = T(0);
 #pragma unroll
       for (int s = 0; s < MAXC; ++s) {
@@ -238,10 +247,10 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
             if (FIRST)
               y[v] = p.mode == 0 ? src[s][v] * scale : src[s][v];
             else
-              y[v] = relu((src[s][v] + ai) - bv[v]);
+              y[v] = relu(subx(addx(src[s][v], ai, one), bv[v], one));
             if (j0 + v >= nc) y[v] = T(0);
-            racc += y[v];
-            cacc[s][v] += y[v];
+            racc = addx(racc, y[v], one);
+            cacc[s][v] = addx(cacc[s][v], y[v], one);
           }
           vec_store<T, VEC>(row + j0, vdst, nc - j0, y);
         }
@@ -274,7 +283,7 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
       const int inext = i + kSdsnWarps;
       if (PREF && inext < nr) load_row(inext, nxt);
       T* row = tile + (size_t)i * ldt;
-      const T ai = FIRST ? T(0) : arow[i] + cS;
+      const T ai = FIRST ? T(0) : addx(arow[i], cS, one);
       T racc = T(0);
 #pragma unroll
       for (int s = 0; s < MAXC; ++s) {
@@ -288,10 +297,10 @@ __device__ __forceinline__ void sdsn_pass(const SdsnK<T, TIn>& p, T* tile, int l
             if (FIRST)
               y[v] = p.mode == 0 ? cur[s][v] * scale : cur[s][v];
             else
-              y[v] = relu((cur[s][v] + ai) - bv[v]);
+              y[v] = relu(subx(addx(cur[s][v], ai, one), bv[v], one));
             if (j0 + v >= nc) y[v] = T(0);
-            racc += y[v];
-            cacc[s][v] += y[v];
+            racc = addx(racc, y[v], one);
+            cacc[s][v] = addx(cacc[s][v], y[v], one);
           }
           vec_store<T, VEC>(row + j0, vdst, nc - j0, y);
         }
@@ -613,6 +622,7 @@ int launch_sdsn_t(const SdsnLaunch& L, int num_sms, cudaStream_t s) {
   k.tc = tc;
   k.resident = resident ? 1 : 0;
   k.mode = L.mode;
+  k.one = 1.0;
   k.X = static_cast<const TIn*>(L.X);
   k.ldx = L.ldx;
   k.Y = static_cast<T*>(L.Y);
@@ -709,6 +719,7 @@ int launch_sdsn_group_t(const SdsnLaunch* L, int count, int max_blocks, void* dd
     k.block0 = block0;
     block0 += P * Q;
     k.mode = L[i].mode;
+    k.one = 1.0;
     k.X = static_cast<const TIn*>(L[i].X);
     k.ldx = L[i].ldx;
     k.Y = static_cast<T*>(L[i].Y);

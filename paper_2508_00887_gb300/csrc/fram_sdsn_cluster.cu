@@ -853,6 +853,7 @@ struct PolishK {
   const SdsnStats* gate;
   double gate_tol;
   SdsnStats* stats;
+  double one;  // 1.0, read at run time (add64)
 };
 
 // max(0, y) on the integer pipe: clear y if its sign bit is set.
@@ -871,6 +872,7 @@ __device__ __forceinline__ void polish_warp_body(const PolishK& p) {
   const int max_sweeps =
       (p.gate != nullptr && p.gate->gamma <= p.gate_tol) ? 0 : p.max_sweeps;
   const double inv_n = 1.0 / (double)n, inv_n2 = inv_n * inv_n;
+  const double one = p.one;
 
   double y[16][NC], rp[16], cacc[NC], bb[NC];
   double cS = 0.0, g = INFINITY;
@@ -884,8 +886,8 @@ __device__ __forceinline__ void polish_warp_body(const PolishK& p) {
       const int j = lane + 32 * c;
       const double v = (i < n && j < n) ? (double)p.X[(size_t)i * p.ldx + j] : 0.0;
       y[r][c] = v;
-      rp[r] = c == 0 ? v : __dadd_rn(rp[r], v);
-      cacc[c] = __dadd_rn(cacc[c], v);
+      rp[r] = c == 0 ? v : add64(rp[r], v, one);
+      cacc[c] = add64(cacc[c], v, one);
     }
   }
 
@@ -900,15 +902,15 @@ __device__ __forceinline__ void polish_warp_body(const PolishK& p) {
     for (int c = 0; c < NC; ++c) {
       double t = s_colp[par][0][lane + 32 * c];
 #pragma unroll
-      for (int q = 1; q < W; ++q) t = __dadd_rn(t, s_colp[par][q][lane + 32 * c]);
+      for (int q = 1; q < W; ++q) t = add64(t, s_colp[par][q][lane + 32 * c], one);
       ct[c] = t;
     }
     const double rs = transpose_reduce16(rp, lane);  // row r0 + (lane >> 1)
     double S = ct[0];
 #pragma unroll
-    for (int c = 1; c < NC; ++c) S = __dadd_rn(S, ct[c]);
+    for (int c = 1; c < NC; ++c) S = add64(S, ct[c], one);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) S = __dadd_rn(S, __shfl_xor_sync(0xffffffffu, S, o));
+    for (int o = 16; o > 0; o >>= 1) S = add64(S, __shfl_xor_sync(0xffffffffu, S, o), one);
 #pragma unroll
     for (int c = 0; c < NC; ++c) bb[c] = lane + 32 * c < n ? __dmul_rn(ct[c], inv_n) : INFINITY;
     __syncwarp();
@@ -927,13 +929,13 @@ __device__ __forceinline__ void polish_warp_body(const PolishK& p) {
     for (int c = 0; c < NC; ++c) cacc[c] = 0.0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const double ai = __dadd_rn(s_a[w][r], cS);
+      const double ai = add64(s_a[w][r], cS, one);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const double t = relu_d(__dsub_rn(__dadd_rn(y[r][c], ai), bb[c]));
+        const double t = relu_d(sub64(add64(y[r][c], ai, one), bb[c], one));
         y[r][c] = t;
-        rp[r] = c == 0 ? t : __dadd_rn(rp[r], t);
-        cacc[c] = __dadd_rn(cacc[c], t);
+        rp[r] = c == 0 ? t : add64(rp[r], t, one);
+        cacc[c] = add64(cacc[c], t, one);
       }
     }
     ++k;
@@ -986,6 +988,7 @@ PolishK make_polish(const SdsnLaunch& L) {
   k.gate = L.gate;
   k.gate_tol = L.gate_tol;
   k.stats = L.stats;
+  k.one = 1.0;
   return k;
 }
 
