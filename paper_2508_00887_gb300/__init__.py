@@ -261,13 +261,47 @@ def fram_solve(ctx, n, A, B, K=None, params=None, X_out=None, perm_out=None, che
     return st, info
 
 
+def _is_index_array(x, itemsize):
+    """A 1-D C-contiguous numpy integer array with `itemsize`-byte entries."""
+    dt = getattr(x, "dtype", None)
+    return (dt is not None and hasattr(x, "ctypes") and getattr(dt, "kind", "") in "iu" and
+            dt.itemsize == itemsize and x.ndim == 1 and x.flags.c_contiguous)
+
+
+def _ptr_table(xs, count, dtype):
+    """The pointer table of one fram_solve_batched argument: an integer
+    address array (numpy, 8-byte entries, one per pair) is passed as it is,
+    with no copy and no per-entry check; a list of tensors / arrays / addresses
+    goes through _addrs.  Returns (argument, object to keep alive)."""
+    if xs is None:
+        return None, None
+    if _is_index_array(xs, 8):
+        if xs.shape[0] != count:
+            raise ValueError("an address array needs one entry per pair")
+        return xs.ctypes.data, xs
+    arr = (_P * count)(*_addrs(xs, dtype))
+    return arr, arr
+
+
 def fram_solve_batched(ctx, ns, As, Bs, params=None, X_outs=None, perm_outs=None, check=True):
+    """ns: a list of sizes or a contiguous numpy int32 array.  As, Bs, X_outs,
+    perm_outs: lists of matrices / vectors, or numpy integer arrays of their
+    addresses (8-byte entries), e.g. base + byte offsets into one packed
+    buffer per batch -- the fast path for large batches, which skips the
+    per-tensor checks (the library still checks every pointer's memory
+    kind)."""
     count = len(ns)
-    n_arr = (C.c_int * count)(*ns)
-    a_arr = (_P * count)(*_addrs(As))
-    b_arr = (_P * count)(*_addrs(Bs))
-    x_arr = (_P * count)(*_addrs(X_outs)) if X_outs is not None else None
-    p_arr = (_P * count)(*_addrs(perm_outs, "int32"))
+    keep = []
+    if _is_index_array(ns, 4):
+        n_arr = ns.ctypes.data
+        keep.append(ns)
+    else:
+        n_arr = (C.c_int * count)(*ns)
+    a_arr, ka = _ptr_table(As, count, "float64")
+    b_arr, kb = _ptr_table(Bs, count, "float64")
+    x_arr, kx = _ptr_table(X_outs, count, "float64")
+    p_arr, kp = _ptr_table(perm_outs, count, "int32")
+    keep += [ka, kb, kx, kp]
     infos = (FramInfo * max(count, 1))()
     st = load().fram_solve_batched(ctx, count, n_arr, a_arr, b_arr,
                                    C.byref(params) if params is not None else None,

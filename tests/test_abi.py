@@ -108,3 +108,24 @@ def test_binding_rejects_wrong_dtypes():
     with pytest.raises(ValueError):
         fr._addr(np.zeros((4, 4))[:, :2])
     assert fr._addr(None) is None
+
+
+def test_binding_takes_address_arrays_as_they_are():
+    # fram_solve_batched's fast path: a numpy array of 8-byte addresses is
+    # handed to the library without a copy; any other length is refused; a
+    # list still goes through the per-entry checks.
+    import numpy as np
+    a = np.arange(5, dtype=np.uint64) * np.uint64(64) + np.uint64(4096)
+    arg, keep = fr._ptr_table(a, 5, "float64")
+    assert arg == a.ctypes.data and keep is a
+    with pytest.raises(ValueError):
+        fr._ptr_table(a, 4, "float64")
+    arg, keep = fr._ptr_table([np.zeros((2, 2)), None], 2, "float64")
+    assert len(arg) == 2 and arg[1] is None and arg is keep
+    with pytest.raises(ValueError):
+        fr._ptr_table([np.zeros((2, 2), dtype=np.float32)], 1, "float64")
+    assert fr._ptr_table(None, 3, "float64") == (None, None)
+    assert fr._is_index_array(np.zeros(3, dtype=np.int32), 4)
+    assert not fr._is_index_array(np.zeros(3, dtype=np.float64), 8)
+    assert not fr._is_index_array(np.zeros((2, 2), dtype=np.uint64), 8)
+    assert not fr._is_index_array([1, 2, 3], 8)

@@ -112,6 +112,36 @@ def test_batched_host_buffers_and_no_x(torch_cuda, ctx):
         assert np.array_equal(a, b) and np.array_equal(c, d) and np.array_equal(c, e)
 
 
+def test_batched_address_arrays_equal_tensor_lists(torch_cuda, ctx):
+    # The fast path of the binding: every argument as a numpy array of
+    # addresses into one packed buffer (sizes as an int32 array), device and
+    # host.  Results are bit-identical to the same batch passed as lists.
+    torch = torch_cuda
+    pairs = fi.keypoint_batch(300, seed=9)
+    params = fr.fram_default_params(theta=2.0, precision=fr.FRAM_PREC_MIXED_TF32)
+    Xl, Pl, il = run_batched(torch, ctx, pairs, params, device=True)
+    ns = np.array([g.n for g in pairs], dtype=np.int32)
+    off_m = np.concatenate([[0], np.cumsum([g.n * g.n for g in pairs])[:-1]]).astype(np.uint64)
+    off_v = np.concatenate([[0], np.cumsum([g.n for g in pairs])[:-1]]).astype(np.uint64)
+    for dev in ("cuda", "cpu"):
+        A = torch.from_numpy(np.concatenate([g.A.ravel() for g in pairs])).to(dev)
+        B = torch.from_numpy(np.concatenate([g.B.ravel() for g in pairs])).to(dev)
+        X = torch.empty(int(sum(g.n * g.n for g in pairs)), dtype=torch.float64, device=dev)
+        P = torch.empty(int(ns.sum()), dtype=torch.int32, device=dev)
+        addr = lambda t, off: np.uint64(t.data_ptr()) + off * np.uint64(t.element_size())
+        _, ia = fr.fram_solve_batched(ctx, ns, addr(A, off_m), addr(B, off_m), params,
+                                      addr(X, off_m), addr(P, off_v))
+        Xh, Ph = X.cpu().numpy(), P.cpu().numpy()
+        for k, g in enumerate(pairs):
+            m, v = int(off_m[k]), int(off_v[k])
+            assert np.array_equal(Xh[m:m + g.n * g.n].reshape(g.n, g.n), Xl[k]), (dev, k)
+            assert np.array_equal(Ph[v:v + g.n], Pl[k]), (dev, k)
+            assert ia[k].outer_iters == il[k].outer_iters
+    with pytest.raises(ValueError):
+        fr.fram_solve_batched(ctx, ns, addr(A, off_m)[:-1], addr(B, off_m), params, None,
+                              addr(P, off_v))
+
+
 def test_batched_host_buffers_large_batch_packed_in_parallel(torch_cuda, ctx):
     # The full 4096-pair keypoint batch from host buffers: its 106 MB of
     # inputs are packed into the staging arena on several threads (batches
