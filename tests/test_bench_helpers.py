@@ -66,3 +66,25 @@ def test_cluster_sdsn_roofline_is_alu_on_the_cluster_sms():
     # above the cluster range the FP32 SDSN streams through HBM
     big = SimpleNamespace(**{**vars(info), "ms_sdsn": 490.0})
     assert bench.roofline([big], 8192, "tf32", {"hbm_gbs": 6800.0}, "measured")["bound"] == "hbm"
+
+
+def test_packed_batch_addresses_and_views():
+    # The batch bench's packed buffers: entry k's address is the buffer base
+    # plus the byte offset of the entries before it, its view holds exactly
+    # that entry, and the address array has one 8-byte entry per pair (the
+    # form the binding passes to the library as it is).
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    rng = np.random.default_rng(3)
+    shapes = [(int(n), int(n)) for n in rng.integers(2, 40, size=17)]
+    src = [rng.random(sh) for sh in shapes]
+    pk = bench.Packed(torch, shapes, torch.float64, "cpu", src=src)
+    assert pk.addr.dtype == np.uint64 and pk.addr.shape == (17,)
+    off = 0
+    for k, (sh, a) in enumerate(zip(shapes, src)):
+        assert int(pk.addr[k]) == pk.buf.data_ptr() + 8 * off
+        assert pk.views[k].data_ptr() == int(pk.addr[k])
+        assert np.array_equal(pk.views[k].numpy(), a)
+        off += sh[0] * sh[1]
+    pv = bench.Packed(torch, [(n,) for n, _ in shapes], torch.int32, "cpu")
+    assert int(pv.addr[1]) - int(pv.addr[0]) == 4 * shapes[0][0]
