@@ -1,6 +1,8 @@
 // SDSN (Alg. 2 of arXiv 2508.00887) in FP32 for 2 <= n <= 1024, held
-// entirely on chip by ONE thread-block cluster of s x s CTAs (s = 1, 2 or 4;
-// 16 CTAs is a non-portable cluster size).
+// entirely on chip: for n <= 64 in the registers of one or two warps (the
+// warp form, further down), above that by ONE thread-block cluster of s x s
+// CTAs (s = 1, 2 or 4; 16 CTAs is a non-portable cluster size).  The mixed
+// paths' FP64 polish of n <= 64 also runs here, in a warp form of its own.
 //
 //   step 1   Y = (theta/2) X / max(X)
 //   sweep    Y_ij <- max(0, Y_ij + 1/n + S/n^2 - r_i/n - c_j/n)      (eq. 7)
