@@ -280,9 +280,10 @@ fram_status fram_sdsn(fram_ctx *ctx, int n, const double *X, double *D, double t
  *      ldd == ldx); the padding columns of either are not touched
  * D0 = (theta/2) X / max(X) (max taken over the n x n block); every sweep
  * D <- max(0, P1(D)) (eq. 7) in FP32 arithmetic with FP32 row and column
- * sums; the total S and gamma = S/n - 1 are formed in FP64 from FP32 tile
- * totals; stop when gamma <= gamma_tol (after at least one sweep) or after
- * max_sweeps sweeps.  sweeps_out / gamma_out (host) may be NULL.
+ * sums; the total S (from FP32 partial totals) and gamma = S/n - 1 carry
+ * about twice FP32's precision: FP64 in the streamed form (n > 1024), a
+ * double-float sum in the on-chip forms; stop when gamma <= gamma_tol
+ * (after at least one sweep) or after max_sweeps sweeps.  sweeps_out / gamma_out (host) may be NULL.
  * Errors: FRAM_ERR_INVALID (bad sizes, strides or pointers),
  * FRAM_ERR_DEGENERATE (max(X) <= 0), FRAM_ERR_TIMEOUT, FRAM_ERR_CUDA. */
 fram_status fram_sdsn_f32(fram_ctx *ctx, int n, const float *X, int ldx, float *D, int ldd,
