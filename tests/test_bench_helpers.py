@@ -88,3 +88,17 @@ def test_packed_batch_addresses_and_views():
         off += sh[0] * sh[1]
     pv = bench.Packed(torch, [(n,) for n, _ in shapes], torch.int32, "cpu")
     assert int(pv.addr[1]) - int(pv.addr[0]) == 4 * shapes[0][0]
+
+
+def test_batch_roofline_counts_the_algorithmic_flops():
+    # Per pair: 4 n^3 + 6 n^2 flops per outer iteration (the two products and
+    # the update with its delta) and 7 n^2 per SDSN sweep, over the call's
+    # time, against the FP32 CUDA-core peak.
+    infos = [SimpleNamespace(outer_iters=3, total_sweeps=50),
+             SimpleNamespace(outer_iters=2, total_sweeps=20)]
+    r = bench.batch_roofline([10, 64], infos, 1e-3)
+    flops = 3 * (4 * 10 ** 3 + 6 * 100) + 50 * 7 * 100 + 2 * (4 * 64 ** 3 + 6 * 64 ** 2) + \
+        20 * 7 * 64 ** 2
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP32_ALU_TFLOPS)
+    assert bench.FP32_ALU_TFLOPS == pytest.approx(152 * 128 * 2 * 2.07 / 1e3)
